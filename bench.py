@@ -1,0 +1,383 @@
+"""Benchmark of the fused LES Runge-Kutta path on GB300.
+
+One step = one time step of the whole path: the CFL time-step reduction, five
+fused residual/update stages and their boundary fills, on the 256 x 192 x 192
+mapped jet grid (9.44e6 points; the paper's scalability workload shape,
+arXiv 2003.09926 Section 5.1).  Throughput is reported in Mpt-stage/s =
+grid points x 5 stages x steps / time / 1e6.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Headline value: FP32 state and fluxes, metric terms generated in FP64 and
+stored in FP32 (P32), inputs resident in HBM, device-timed with CUDA events
+on the grid's stream.  Also reported: P32_M64 (FP64-stored metrics; the flux
+arithmetic consumes them in FP32, so its results equal P32's) and plain FP64
+(P64) variants, the FP32 error against FP64 on the same workload, the fused stage kernel against the
+measured HBM roofline, an end-to-end number through the public C ABI with
+host buffers, and the CPU FP64 oracle timed on the host cores.
+
+Under torchrun (N > 1) every rank advances its own independent grid (the
+batched/served workloads shard by grid with no data exchange): weak scaling,
+value = points x stages x steps summed over ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpt-stage/s FP32-batched vs plain FP64 at stated err; HBM GB/s; p50/p99 latency"
+UNIT = "Mpt-stage/s"
+HBM_FALLBACK_GBS = 6800.0
+# algorithmic bytes per point-stage of the fused stage kernel: reads of
+# Q^(l-1) and Q^(0), write of Q^(l) (5 values each), metric terms S (9) + J;
+# stage 1 reads Q^(0) once, so the 5-stage average is (4 x full + 1 x less) / 5
+ES = {0: 8, 1: 4, 2: 4}
+MS = {0: 8, 1: 8, 2: 4}
+
+
+def bytes_per_point_stage(prec: int) -> float:
+    es, ms = ES[prec], MS[prec]
+    full = 15 * es + 10 * ms
+    first = 10 * es + 10 * ms
+    return (4 * full + first) / 5.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max((num(r[2]) or 0.0) for r in self.rows)}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def stage_traffic(prec: int):
+    """DRAM bytes per point-stage of the stage kernel from a committed ncu
+    capture, if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2003_09926_gb300", "csrc", "jz_stage.cu")
+    p = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    try:
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        with open(p) as fh:
+            rec = json.load(fh)
+        ent = rec.get(str(prec))
+        if ent and ent.get("kernel_sha256") == sha:
+            return float(ent["bytes_per_point_stage"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def interior_points(grid: dict) -> int:
+    n = 1
+    for a, key in enumerate(("ni", "nj", "nk")):
+        per = grid["bc"][2 * a] == 0
+        n *= grid[key] if per else grid[key] - 2
+    return n
+
+
+def time_steps(jz, torch, g, steps: int, cfl: float, world: int, profile: bool):
+    """Device time of `steps` steps (CUDA events on the grid's stream), max over ranks."""
+    dist = torch.distributed
+    launches0 = jz.jz_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if profile:
+        jz.jz_profile_begin(g.h)
+    ev0.record(g.stream)
+    for _ in range(steps):
+        g.step(cfl=cfl)
+    ev1.record(g.stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = jz.jz_launch_count() - launches0
+    prof = None
+    if profile:
+        prof = jz.jz_profile_read(g.h)
+        jz.jz_profile_end(g.h)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, launches, prof
+
+
+def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
+    """The oracle as it stands on the host cores: one RK step of the same jet
+    workload, timed (metric generation excluded)."""
+    import oracle
+    from paper_2003_09926_gb300 import workloads as W
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    grid = W.jet_grid(*sample_shape, map_amp=cfg["grid"]["map_amp"], map_seed=cfg["grid"]["map_seed"])
+    o = oracle.Oracle(grid, cfg["flow"])
+    Q = o.init(cfg["seed"])
+    t0 = time.perf_counter()
+    o.step(Q, cfl=cfg["cfl"])
+    sec = time.perf_counter() - t0
+    pts = interior_points(grid)
+    return {"value": pts * 5 / sec / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one RK step (5 stages) of the {sample_shape[0]}x{sample_shape[1]}x{sample_shape[2]} mapped jet "
+                      f"grid in FP64, OpenMP over k-planes, {sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU FP64 oracle on the host cores, same metric."""
+    if rank != 0:
+        return 0
+    from paper_2003_09926_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    cfg = W.config1()
+    shape = (64, 48, 48)  # bounded sample of the 256x192x192 workload per step
+    grid = W.jet_grid(*shape, map_amp=cfg["grid"]["map_amp"], map_seed=cfg["grid"]["map_seed"])
+    o = oracle.Oracle(grid, cfg["flow"])
+    Q = o.init(cfg["seed"])
+    for _ in range(args.warmup):
+        o.step(Q, cfl=cfg["cfl"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(Q, cfl=cfg["cfl"])
+    sec = time.perf_counter() - t0
+    pts = interior_points(grid)
+    value = pts * 5 * args.steps / sec / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c1_jet_256x192x192 (per step: 64x48x48 sample of the same jet and mapping)",
+                       "precision": "FP64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} RK steps of a 64x48x48 sample of the mapped jet workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (default steps/10)")
+    args = ap.parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    from paper_2003_09926_gb300 import build as B
+    from paper_2003_09926_gb300 import jz
+    from paper_2003_09926_gb300 import workloads as W
+
+    B.build()
+    jz.lib()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    head = W.P32
+    cfg = W.config1(precision=head)
+    grid = cfg["grid"]
+    pts = interior_points(grid)
+    results = {}
+    clocks = None
+    prof = None
+    launches = 0
+    for prec in (head, W.P32_M64, W.P64):
+        g = jz.Grid(dict(grid, precision=prec), device=local).init(cfg["flow"], cfg["seed"] + rank)
+        steps = args.steps if prec != W.P64 else (args.fp64_steps or max(3, args.steps // 10))
+        for _ in range(args.warmup):
+            g.step(cfl=cfg["cfl"])
+        torch.cuda.synchronize()
+        if prec == head:
+            with ClockSampler(local) as cs:
+                ms, launches, prof = time_steps(jz, torch, g, steps, cfg["cfl"], world, profile=True)
+            clocks = cs.summary()
+        else:
+            ms, _, _ = time_steps(jz, torch, g, steps, cfg["cfl"], world, profile=False)
+        results[prec] = {"ms_per_step": ms / steps, "steps": steps,
+                         "value": world * pts * 5 * steps / (ms / 1e3) / 1e6}
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+
+    # FP32 error against FP64 on this workload after 20 steps from the same state
+    err_steps = 20
+    ref = jz.Grid(dict(grid, precision=W.P64), device=local).init(cfg["flow"], cfg["seed"])
+    ref.nsteps(err_steps, cfl=cfg["cfl"])
+    Qref = ref.download()
+    ref.close()
+    del ref
+    errors = {}
+    for prec in (W.P32_M64, W.P32):
+        g = jz.Grid(dict(grid, precision=prec), device=local).init(cfg["flow"], cfg["seed"])
+        g.nsteps(err_steps, cfl=cfg["cfl"])
+        Q = g.download()
+        g.close()
+        inner = (slice(3, -3),) * 3
+        errors[W.PRECISION_NAMES[prec]] = {
+            "max_rel_interior": max(float(np.abs(Q[v][inner] - Qref[v][inner]).max() / np.abs(Qref[v]).max())
+                                    for v in range(5)),
+            "max_rel_all_nodes": max(float(np.abs(Q[v] - Qref[v]).max() / np.abs(Qref[v]).max()) for v in range(5)),
+            "l2_rel": max(float(np.sqrt(np.mean((Q[v] - Qref[v]) ** 2) / np.mean(Qref[v] ** 2))) for v in range(5))}
+        del g
+    del Qref
+
+    # end to end through the public C ABI with host buffers: the initial state
+    # uploaded from pinned host memory, every step followed by the
+    # diagnostics read-back (the step's metric), the final state downloaded
+    g = jz.Grid(dict(grid, precision=head), device=local).init(cfg["flow"], cfg["seed"] + rank)
+    host_in = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
+    g.download(host_in)
+    for _ in range(args.warmup):
+        g.step(cfl=cfg["cfl"])
+        g.diagnostics()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.upload(host_in)
+    for _ in range(args.steps):
+        g.step(cfl=cfg["cfl"])
+        g.diagnostics()
+    g.download(host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    state_bytes = host_in.nbytes
+    diag_bytes = 256
+    e2e = {"value": world * pts * 5 * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / args.steps,
+           "d2h_bytes_per_step": diag_bytes + state_bytes / args.steps,
+           "note": "initial state uploaded from pinned host memory, diagnostics read back every step, "
+                   "final state downloaded"}
+    g.close()
+
+    # roofline of the fused stage kernel (dominant kernel) in the headline run
+    peak, peak_kind = measured_hbm_peak()
+    ms_k, n_k = prof[0][0], prof[1][0]
+    stage_ms = ms_k / max(1, n_k)
+    bpps = bytes_per_point_stage(head)
+    achieved = bpps * pts / (stage_ms / 1e3) / 1e9
+    tr = stage_traffic(head)
+    total_ms = sum(prof[0])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tr * pts) if tr else None, "peak_kind": peak_kind,
+                "kernel": "k_stage (fused RK stage)", "algorithmic_bytes_per_point_stage": bpps,
+                "points_per_launch": pts, "avg_launch_ms": stage_ms,
+                "share_of_step": ms_k / total_ms if total_ms else None,
+                "other_kernels_ms": {"boundary_fill": prof[0][1], "timestep": prof[0][2]}}
+
+    line = {"metric": METRIC, "value": results[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c1_jet_256x192x192 mapped jet, FP32 state/flux, FP64-generated FP32 metrics (P32)",
+                       "grid": [grid["ni"], grid["nj"], grid["nk"]], "points_updated": pts,
+                       "precision": "P32", "parallelism": f"{world} independent grid(s), one per GPU",
+                       "l2": "inputs larger than L2 (state + metrics 1.0 GB per grid)"},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+            "variants": {W.PRECISION_NAMES[p]: r for p, r in results.items()},
+            "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
+                                   "interior": "nodes at least 3 from every face; far-field face nodes can differ by O(1) where the Riemann condition switches branch (sign of u_n, |u_n| = c) between precisions"},
+            "fp64_vs_fp32_speedup": results[head]["value"] / results[W.P64]["value"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * jz.h -- C ABI of the GB300 (sm_103a) implementation of the per-stage
+ * residual and explicit 5-stage Runge-Kutta update of the filtered
+ * compressible Navier-Stokes (LES) equations on a structured curvilinear
+ * grid, after "On the Scalability of CFD Tool for Supersonic Jet Flow
+ * Configurations" (arXiv 2003.09926).
+ *
+ *   Section 3, Eqs. les / vec-les / con-prop   the conservation law dQ/dt = -RHS
+ *   Section 3, Eq. 2, Eq. q_mod, Eq. sutherland, Eq. tau_mod
+ *                                               gas model and viscous terms
+ *   Section 3 (numerical method paragraph)      centred 2nd-order fluxes in general
+ *                                               curvilinear coordinates, anisotropic
+ *                                               scalar dissipation (Turkel & Vatsa),
+ *                                               explicit 5-stage Runge-Kutta
+ *   Section 3 (boundary-condition paragraph)    supersonic inflow, Riemann far field
+ *   Section 4.2, Fig. jazzy                     per stage: boundary update,
+ *                                               inviscid flux, dissipation, viscous flux
+ *   Section 4.3                                 two-layer ghost fringe, five-point stencil
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: JZ_OK (0) or a negative JZ_E* code.
+ *    No C++ exception crosses this boundary.  jz_last_error() returns the
+ *    calling thread's message for its last failing call.
+ *  - Device memory and the CUDA stream belong to the caller.  The library
+ *    carves its arrays out of one caller-provided device buffer of
+ *    jz_grid_bytes() bytes and never allocates, frees or resizes device
+ *    memory on its own.  Host buffers also belong to the caller.
+ *  - Work is enqueued asynchronously on the grid's stream unless a function
+ *    says it synchronises.  The time step stays on the device.
+ *  - Units are non-dimensional: freestream density, sound speed and
+ *    temperature 1, jet diameter 1, freestream pressure 1/gamma, jet
+ *    velocity = Mach number, viscosity at freestream temperature = mach / re.
+ */
+#ifndef JZ_H
+#define JZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define JZ_OK 0
+#define JZ_EINVAL (-1)     /* bad argument, descriptor or call order      */
+#define JZ_ENOMEM (-2)     /* caller buffer too small / over budget        */
+#define JZ_ECUDA (-3)      /* a CUDA runtime call failed                   */
+#define JZ_ENONFINITE (-4) /* state holds non-finite values                */
+#define JZ_ETIMEOUT (-5)   /* a bounded device wait gave up                */
+
+/* boundary kinds per face (faces ordered x-, x+, y-, y+, z-, z+).  A
+ * direction is periodic when both of its faces are JZ_BC_PERIODIC. */
+#define JZ_BC_PERIODIC 0
+#define JZ_BC_INFLOW 1   /* jet exit plane: fixed top-hat profile (Section 3) */
+#define JZ_BC_FARFIELD 2 /* Riemann invariants against air at rest (Section 3) */
+
+/* precision modes: state/flux arithmetic, metric storage */
+#define JZ_P64 0     /* FP64 state and fluxes, FP64 metrics                   */
+#define JZ_P32_M64 1 /* FP32 state and fluxes, FP64-stored metrics             */
+#define JZ_P32 2     /* FP32 state and fluxes, FP64-generated FP32 metrics     */
+
+/* initial conditions */
+#define JZ_IC_JET 0       /* top-hat jet column plus seeded velocity noise     */
+#define JZ_IC_QUIESCENT 1 /* air at rest (Section 5.1: the paper's start state) */
+
+/* Grid descriptor.  Nodes are numbered 0..n-1 per direction (i fastest);
+ * non-periodic directions need n >= 3 and their first and last nodes are
+ * boundary nodes set by the boundary conditions.  Coordinates: x is uniform
+ * on [lo[0], hi[0]]; y and z (when not periodic and stretch_c > 0) follow a
+ * tanh clustering about |y| = cluster_r; every coordinate then receives a
+ * seeded sinusoidal offset of amplitude map_amp x local spacing (0 = none).
+ * Periodic directions use uniform spacing (hi - lo)/n. */
+typedef struct jz_grid_desc {
+  int ni, nj, nk;
+  int bc[6];
+  double lo[3], hi[3];
+  double cluster_r, stretch_c, stretch_w;
+  double map_amp;
+  uint64_t map_seed;
+  int precision; /* JZ_P64, JZ_P32_M64 or JZ_P32 */
+} jz_grid_desc;
+
+/* Flow parameters.  re <= 0 means inviscid (no molecular viscosity);
+ * cs = 0 disables the Smagorinsky eddy viscosity; k2, k4, sigma are the
+ * dissipation constants; s1 is the Sutherland constant over T_inf; r0 and
+ * theta shape the jet profile u = (M/2)(1 - tanh((r - r0)/(2 theta))); noise
+ * is the velocity-noise amplitude relative to the jet velocity. */
+typedef struct jz_flow_params {
+  double mach, re, gamma, pr, prt, cs, k2, k4, sigma, s1, r0, theta, noise;
+  int ic; /* JZ_IC_JET or JZ_IC_QUIESCENT */
+} jz_flow_params;
+
+/* Diagnostics over all grid nodes (ghosts excluded), in FP64, summed in a
+ * fixed order (bitwise reproducible run to run). */
+typedef struct jz_diag {
+  double time;      /* simulated time                                  */
+  int64_t step;     /* completed time steps                            */
+  double dt;        /* last time step                                  */
+  double sum[5];    /* sum over nodes of Q_v / J (conserved integrals) */
+  double rho_min, rho_max, p_min, p_max;
+  double mach_max;  /* max |u| / c                                     */
+  int64_t nonfinite;/* nodes with a non-finite conserved value         */
+} jz_diag;
+
+typedef struct jz_grid jz_grid;
+typedef struct jz_batch jz_batch;
+
+/* Copy the calling thread's last error message into buf (always
+ * NUL-terminated when len > 0).  Returns the message length. */
+int jz_last_error(char* buf, size_t len);
+
+/* Device bytes a grid with this descriptor needs (state x3, metrics,
+ * coordinate tables, reduction scratch).  Pure arithmetic: used for
+ * HBM-budget admission.  JZ_EINVAL on a bad descriptor. */
+int jz_grid_bytes(const jz_grid_desc* desc, size_t* bytes);
+
+/* Create a grid in a caller-owned device buffer (>= jz_grid_bytes, 256-byte
+ * aligned) on the caller's stream (cudaStream_t passed as void*; NULL =
+ * legacy default stream) and enqueue the metric generation: analytic
+ * coordinates, then the conservative metric terms S^k_m = (d xi_k/d x_m)/J
+ * and J at every node, in FP64 (Section 3: generalised curvilinear
+ * transformation; Section 4.2: Jacobian and metric terms computed once).
+ * The handle is host memory owned by the library until jz_grid_destroy. */
+int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* stream, jz_grid** out);
+
+/* Release the handle (and any captured graph).  Does not free dev_buf. */
+int jz_grid_destroy(jz_grid* g);
+
+/* Set the flow parameters and enqueue the initial state (JZ_IC_JET: top-hat
+ * profile plus noise drawn from SplitMix64(seed ^ (3 lin + m)); or air at
+ * rest), then the boundary conditions.  Resets time and step to 0. */
+int jz_state_init(jz_grid* g, const jz_flow_params* flow, uint64_t seed);
+
+/* Enqueue one time step: the time step from the CFL condition (cfl > 0) or
+ * the fixed dt_fixed (> 0; exactly one of the two must be positive), then
+ * five Runge-Kutta stages Q^(l) = Q^(0) - alpha_l dt J R(Q^(l-1)) with
+ * alpha = 1/4, 1/6, 3/8, 1/2, 1, boundary conditions before every stage
+ * (Section 3; Section 4.2, Fig. jazzy).  Asynchronous; no host sync. */
+int jz_rk_step(jz_grid* g, double cfl, double dt_fixed);
+
+/* Enqueue n steps as replays of a CUDA graph of one step (captured on first
+ * use and re-captured when cfl / dt_fixed change).  Asynchronous. */
+int jz_nsteps(jz_grid* g, int n, double cfl, double dt_fixed);
+
+/* Compute diagnostics on the device, copy them to *out.  Synchronises the
+ * grid's stream.  Returns JZ_ENONFINITE (with *out filled) when any grid
+ * node holds a non-finite value. */
+int jz_diagnostics(jz_grid* g, jz_diag* out);
+
+/* Copy the state to host memory: n = 5*ni*nj*nk doubles, layout [v][k][j][i]
+ * (conserved rho, rho u, rho v, rho w, e), ghosts excluded; FP32 states are
+ * widened.  Synchronises the stream. */
+int jz_state_download(jz_grid* g, double* host, size_t n);
+
+/* Replace the state from host memory (layout as jz_state_download; values
+ * at boundary nodes are overwritten by the boundary conditions, which are
+ * applied after the upload).  Requires jz_state_init to have set the flow
+ * parameters.  Synchronises the stream (host buffer may be reused on return). */
+int jz_state_upload(jz_grid* g, const double* host, size_t n);
+
+/* Batched execution of many grids in one launch per stage.  The batch
+ * borrows the grids (which must share one precision mode and have flow
+ * parameters set) and a caller-owned device buffer of jz_batch_bytes bytes
+ * for its tile table; work goes to `stream`.  Every grid keeps its own CFL
+ * time step, kept on the device. */
+int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes);
+int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out);
+/* Enqueue n steps of every grid in the batch (graph-captured; asynchronous). */
+int jz_batch_nsteps(jz_batch* b, int n, double cfl);
+int jz_batch_destroy(jz_batch* b);
+
+/* --- measurement helpers -------------------------------------------------- */
+
+/* Number of kernel launches this library has issued in this process
+ * (graph replays count every kernel node they run). */
+int jz_launch_count(uint64_t* out);
+
+/* Per-kernel timing with CUDA events recorded on the grid's stream around
+ * every launch jz_rk_step makes while profiling is on (jz_nsteps graphs are
+ * not instrumented).  jz_profile_read synchronises the stream and returns,
+ * per kernel class (0 = fused RK stage, 1 = boundary fill, 2 = time step,
+ * 3 = other), the total milliseconds and launch count since jz_profile_begin. */
+int jz_profile_begin(jz_grid* g);
+int jz_profile_read(jz_grid* g, double ms[4], int64_t launches[4]);
+int jz_profile_end(jz_grid* g);
+
+/* Tile shape of the fused stage kernel for this grid (for tuning and for
+ * the batched tile table): ti x tj nodes per CTA, kc planes per CTA chunk.
+ * jz_set_tiling may change kc (planes per chunk, >= 1); the tile shape is
+ * fixed per precision mode. */
+int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
+int jz_set_tiling(jz_grid* g, int kc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JZ_H */

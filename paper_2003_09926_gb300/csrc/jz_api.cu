@@ -1,0 +1,592 @@
+// jz_api.cu -- host side of the C ABI declared in include/jz.h: descriptor
+// validation, carving of the caller's device buffer, the per-step launch
+// sequence, CUDA-graph replay, diagnostics and host<->device state copies.
+//
+// Per time step (arXiv 2003.09926, Section 4.2, Fig. jazzy; the ghost
+// exchanges of the paper become the boundary fill of the two-layer fringe):
+//   time step (CFL reduction or fixed dt)
+//   stage 1: Q0 -> QA     [boundary fill of QA]
+//   stage 2: QA -> QB     [boundary fill of QB]
+//   stage 3: QB -> QA     [boundary fill of QA]
+//   stage 4: QA -> QB     [boundary fill of QB]
+//   stage 5: QB -> Q0 (in place: each node reads its own Q0 before writing)
+//   boundary fill of Q0
+// Stage 1 needs no boundary fill: Q^n already carries its boundary values,
+// which depend only on interior nodes.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "jz_internal.h"
+
+namespace jz {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static thread_local std::string g_error;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+#define JZ_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(JZ_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carve {
+  Layout L;
+  size_t es, ms;  // state / metric element sizes
+  size_t off_sc, off_partial, off_tab, off_q0, off_qa, off_qb, off_m, total;
+  size_t tab_len;
+};
+
+static int validate(const jz_grid_desc* d) {
+  if (!d) return fail(JZ_EINVAL, "null descriptor");
+  int n[3] = {d->ni, d->nj, d->nk};
+  for (int a = 0; a < 3; ++a) {
+    int b0 = d->bc[2 * a], b1 = d->bc[2 * a + 1];
+    for (int b : {b0, b1})
+      if (b != JZ_BC_PERIODIC && b != JZ_BC_INFLOW && b != JZ_BC_FARFIELD)
+        return fail(JZ_EINVAL, "bad boundary kind %d", b);
+    if ((b0 == JZ_BC_PERIODIC) != (b1 == JZ_BC_PERIODIC))
+      return fail(JZ_EINVAL, "direction %d: both faces or neither must be periodic", a);
+    bool per = b0 == JZ_BC_PERIODIC;
+    if (per ? n[a] < 1 : n[a] < 3) return fail(JZ_EINVAL, "direction %d: %d nodes is too few", a, n[a]);
+    if (n[a] > (1 << 24)) return fail(JZ_EINVAL, "direction %d: %d nodes is too many", a, n[a]);
+    if (!(d->hi[a] > d->lo[a])) return fail(JZ_EINVAL, "direction %d: empty extent", a);
+  }
+  if (d->precision != JZ_P64 && d->precision != JZ_P32_M64 && d->precision != JZ_P32)
+    return fail(JZ_EINVAL, "bad precision mode %d", d->precision);
+  if (d->stretch_c != 0.0 && !(d->stretch_w > 0.0)) return fail(JZ_EINVAL, "stretch_w must be > 0");
+  if (!std::isfinite(d->map_amp) || !std::isfinite(d->stretch_c) || !std::isfinite(d->cluster_r))
+    return fail(JZ_EINVAL, "non-finite grid parameter");
+  return JZ_OK;
+}
+
+static Carve carve(const jz_grid_desc* d) {
+  Carve c;
+  Layout& L = c.L;
+  L.n[0] = d->ni; L.n[1] = d->nj; L.n[2] = d->nk;
+  for (int f = 0; f < 6; ++f) L.bc[f] = d->bc[f];
+  for (int a = 0; a < 3; ++a) {
+    L.per[a] = d->bc[2 * a] == JZ_BC_PERIODIC;
+    L.lo[a] = L.per[a] ? 0 : 1;
+    L.hi[a] = L.per[a] ? L.n[a] - 1 : L.n[a] - 2;
+  }
+  L.pitch = ((d->ni + 2 * NG) + 31) / 32 * 32;
+  L.plane = (long long)L.pitch * (d->nj + 2 * NG);
+  L.npad = L.plane * (d->nk + 2 * NG);
+  c.es = d->precision == JZ_P64 ? 8 : 4;
+  c.ms = d->precision == JZ_P32 ? 4 : 8;
+  c.tab_len = 0;
+  for (int a = 0; a < 3; ++a) c.tab_len += 5 * (size_t)(L.n[a] + 2 * NG);
+  size_t off = 0;
+  c.off_sc = off; off = align256(off + sizeof(Scalars));
+  c.off_partial = off; off = align256(off + sizeof(double) * RED_BLOCKS * DIAG_WORDS);
+  c.off_tab = off; off = align256(off + sizeof(double) * c.tab_len);
+  size_t qbytes = align256(5 * (size_t)L.npad * c.es);
+  c.off_q0 = off; off += qbytes;
+  c.off_qa = off; off += qbytes;
+  c.off_qb = off; off += qbytes;
+  c.off_m = off; off += align256(10 * (size_t)L.npad * c.ms);
+  c.total = off;
+  return c;
+}
+
+struct EventPair { cudaEvent_t a, b; int cls; };
+
+}  // namespace jz
+
+using namespace jz;
+
+struct jz_grid {
+  jz_grid_desc desc;
+  jz_flow_params flow;
+  bool have_flow = false;
+  cudaStream_t stream = nullptr;
+  Carve cv;
+  GridDev dev;
+  char* base = nullptr;
+  // graph of one step
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  double graph_cfl = -1.0, graph_dt = -1.0;
+  uint64_t graph_kernels = 0;
+  // profiling
+  bool profiling = false;
+  std::vector<EventPair> events;
+  std::vector<cudaEvent_t> pool;
+};
+
+struct jz_batch {
+  std::vector<jz_grid*> grids;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  double graph_cfl = -1.0;
+  uint64_t graph_kernels = 0;
+};
+
+namespace {
+
+cudaEvent_t take_event(jz_grid* g) {
+  if (!g->pool.empty()) {
+    cudaEvent_t e = g->pool.back();
+    g->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Enqueue `fn` (a launch) with optional profiling events around it.
+template <typename Fn>
+int timed(jz_grid* g, int cls, Fn fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (g->profiling) {
+    a = take_event(g);
+    b = take_event(g);
+    if (!a || !b) return fail(JZ_ECUDA, "cudaEventCreate failed");
+    JZ_CUDA(cudaEventRecord(a, g->stream));
+  }
+  cudaError_t e = fn();
+  if (e != cudaSuccess) return fail(JZ_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  if (g->profiling) {
+    JZ_CUDA(cudaEventRecord(b, g->stream));
+    g->events.push_back({a, b, cls});
+  }
+  return JZ_OK;
+}
+
+int enqueue_step(jz_grid* g, double cfl, double dt_fixed) {
+  GridDev& d = g->dev;
+  cudaStream_t s = g->stream;
+  int rc;
+  if ((rc = timed(g, 2, [&] { return launch_timestep(d, cfl, dt_fixed, s); }))) return rc;
+  const int src[5] = {0, 1, 2, 1, 2};  // Q0, QA, QB, QA, QB
+  void* dst[5] = {d.QA, d.QB, d.QA, d.QB, d.Q0};
+  for (int l = 0; l < 5; ++l) {
+    if ((rc = timed(g, 0, [&] { return launch_stage(d, l, src[l], dst[l], s); }))) return rc;
+    if ((rc = timed(g, 1, [&] { return launch_bc(d, dst[l], s); }))) return rc;
+  }
+  return JZ_OK;
+}
+
+int check_grid(jz_grid* g, bool need_flow) {
+  if (!g) return fail(JZ_EINVAL, "null grid");
+  if (need_flow && !g->have_flow) return fail(JZ_EINVAL, "flow parameters not set (call jz_state_init first)");
+  return JZ_OK;
+}
+
+int check_dt(double cfl, double dt_fixed) {
+  bool a = cfl > 0.0 && std::isfinite(cfl), b = dt_fixed > 0.0 && std::isfinite(dt_fixed);
+  if (a == b) return fail(JZ_EINVAL, "exactly one of cfl (%g) and dt_fixed (%g) must be positive", cfl, dt_fixed);
+  return JZ_OK;
+}
+
+// planes per CTA chunk: minimise (waves of resident CTAs) x (planes + prologue)
+int default_kc(const Layout& L, int prec) {
+  StageTiling t = stage_tiling(prec);
+  long long tiles = (long long)((L.hi[0] + t.ti) / t.ti) * ((L.hi[1] + t.tj) / t.tj);
+  int nz = L.hi[2] - L.lo[2] + 1;
+  long long slots = 152LL;  // one stage CTA per SM
+  int best = nz;
+  double best_cost = 1e300;
+  for (int kc = 1; kc <= nz; ++kc) {
+    long long ctas = tiles * ((nz + kc - 1) / kc);
+    long long waves = (ctas + slots - 1) / slots;
+    double cost = (double)waves * (kc + 3.0);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = kc; }
+  }
+  return best;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 4-D map over a field array [fields][k][j][i-row of pitch]: box = one plane of
+// (ti+4) x (tj+4) nodes (tile plus two-node halo) x all fields.  Coordinates
+// outside the array read as zero.
+int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int fields, int prec) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  StageTiling t = stage_tiling(prec);
+  const size_t es = fp64 ? 8 : 4;
+  cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.n[1] + 2 * NG), (cuuint64_t)(L.n[2] + 2 * NG),
+                        (cuuint64_t)fields};
+  cuuint64_t strides[3] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.npad * es};
+  cuuint32_t box[4] = {(cuuint32_t)(t.ti + 4), (cuuint32_t)(t.tj + 4), 1, (cuuint32_t)fields};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return JZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jz_last_error(char* buf, size_t len) {
+  if (buf && len > 0) {
+    size_t n = g_error.size() < len - 1 ? g_error.size() : len - 1;
+    memcpy(buf, g_error.data(), n);
+    buf[n] = 0;
+  }
+  return (int)g_error.size();
+}
+
+int jz_grid_bytes(const jz_grid_desc* desc, size_t* bytes) {
+  int rc = validate(desc);
+  if (rc) return rc;
+  if (!bytes) return fail(JZ_EINVAL, "null output");
+  *bytes = carve(desc).total;
+  return JZ_OK;
+}
+
+int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* stream, jz_grid** out) {
+  int rc = validate(desc);
+  if (rc) return rc;
+  if (!out) return fail(JZ_EINVAL, "null output");
+  *out = nullptr;
+  Carve cv = carve(desc);
+  if (!dev_buf) return fail(JZ_EINVAL, "null device buffer");
+  if (((uintptr_t)dev_buf & 255) != 0) return fail(JZ_EINVAL, "device buffer must be 256-byte aligned");
+  if (bytes < cv.total) return fail(JZ_ENOMEM, "device buffer holds %zu bytes, grid needs %zu", bytes, cv.total);
+  static bool configured = false;
+  if (!configured) {
+    JZ_CUDA(stage_configure());
+    configured = true;
+  }
+  jz_grid* g = new (std::nothrow) jz_grid();
+  if (!g) return fail(JZ_ENOMEM, "host allocation failed");
+  g->desc = *desc;
+  g->stream = (cudaStream_t)stream;
+  g->cv = cv;
+  g->base = (char*)dev_buf;
+  GridDev& d = g->dev;
+  d.L = cv.L;
+  d.prec = desc->precision;
+  d.Q0 = g->base + cv.off_q0;
+  d.QA = g->base + cv.off_qa;
+  d.QB = g->base + cv.off_qb;
+  d.M = g->base + cv.off_m;
+  d.sc = (Scalars*)(g->base + cv.off_sc);
+  d.partial = (double*)(g->base + cv.off_partial);
+  d.kc = default_kc(cv.L, d.prec);
+  memset(&d.F, 0, sizeof(d.F));
+  // coordinate tables
+  double* tab = (double*)(g->base + cv.off_tab);
+  long long off = 0;
+  for (int a = 0; a < 3; ++a) {
+    d.C.base[a] = tab + off; off += cv.L.n[a] + 2 * NG;
+    d.C.h[a] = tab + off; off += cv.L.n[a] + 2 * NG;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int e = 0; e < 3; ++e) { d.C.sn[a][e] = tab + off; off += cv.L.n[e] + 2 * NG; }
+  d.C.amp = desc->map_amp;
+  TabParams tp;
+  for (int a = 0; a < 3; ++a) {
+    tp.n[a] = cv.L.n[a];
+    tp.per[a] = cv.L.per[a];
+    tp.lo[a] = desc->lo[a];
+    tp.hi[a] = desc->hi[a];
+  }
+  tp.cluster_r = desc->cluster_r;
+  tp.stretch_c = desc->stretch_c;
+  tp.stretch_w = desc->stretch_w;
+  tp.amp = desc->map_amp;
+  // mapping wave numbers (1..3) and phases drawn from SplitMix64(map_seed ^ c)
+  for (int a = 0; a < 3; ++a)
+    for (int e = 0; e < 3; ++e) {
+      uint64_t c = (uint64_t)(3 * a + e);
+      tp.m[3 * a + e] = 1 + (int)(splitmix64(desc->map_seed ^ (2 * c)) % 3ULL);
+      tp.th[3 * a + e] = 2.0 * 3.14159265358979323846 * unit53(splitmix64(desc->map_seed ^ (2 * c + 1)));
+    }
+  const bool st64 = d.prec == JZ_P64, mt64 = d.prec != JZ_P32;
+  if ((rc = make_plane_map(&d.tmQ[0], d.Q0, st64, cv.L, 5, d.prec)) ||
+      (rc = make_plane_map(&d.tmQ[1], d.QA, st64, cv.L, 5, d.prec)) ||
+      (rc = make_plane_map(&d.tmQ[2], d.QB, st64, cv.L, 5, d.prec)) ||
+      (rc = make_plane_map(&d.tmM, d.M, mt64, cv.L, 10, d.prec))) {
+    delete g;
+    return rc;
+  }
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(d.sc, 0, sizeof(Scalars), g->stream)) != cudaSuccess ||
+      (e = launch_tables(tp, tab, g->stream)) != cudaSuccess || (e = launch_metrics(d, g->stream)) != cudaSuccess) {
+    delete g;
+    return fail(JZ_ECUDA, "grid set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return JZ_OK;
+}
+
+int jz_grid_destroy(jz_grid* g) {
+  if (!g) return JZ_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (auto& p : g->events) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : g->pool) cudaEventDestroy(e);
+  delete g;
+  return JZ_OK;
+}
+
+int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!f) return fail(JZ_EINVAL, "null flow parameters");
+  if (!(f->gamma > 1.0) || !(f->pr > 0.0) || !(f->prt > 0.0) || !(f->mach >= 0.0) || !(f->k2 >= 0.0) ||
+      !(f->k4 >= 0.0) || !(f->sigma > 0.0) || !(f->s1 > 0.0) || !(f->cs >= 0.0) || !(f->theta > 0.0) ||
+      !std::isfinite(f->re) || (f->ic != JZ_IC_JET && f->ic != JZ_IC_QUIESCENT))
+    return fail(JZ_EINVAL, "bad flow parameters");
+  g->flow = *f;
+  g->have_flow = true;
+  FlowC& F = g->dev.F;
+  F.gamma = f->gamma;
+  F.gm1 = f->gamma - 1.0;
+  F.cp = 1.0 / (f->gamma - 1.0);
+  F.mu_inf = f->re > 0.0 ? f->mach / f->re : 0.0;
+  F.s1 = f->s1;
+  F.pr = f->pr;
+  F.prt = f->prt;
+  F.cs = f->cs;
+  F.k2 = f->k2;
+  F.k4 = f->k4;
+  F.sigma = f->sigma;
+  F.mach = f->mach;
+  F.r0 = f->r0;
+  F.theta = f->theta;
+  F.noise = f->noise;
+  F.ic = f->ic;
+  F.viscous = (F.mu_inf > 0.0 || F.cs > 0.0) ? 1 : 0;
+  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+  if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
+  g->graph_cfl = g->graph_dt = -1.0;
+  JZ_CUDA(cudaMemsetAsync(g->dev.sc, 0, sizeof(Scalars), g->stream));
+  JZ_CUDA(launch_init(g->dev, seed, g->stream));
+  JZ_CUDA(launch_bc(g->dev, g->dev.Q0, g->stream));
+  return JZ_OK;
+}
+
+int jz_rk_step(jz_grid* g, double cfl, double dt_fixed) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (int rc = check_dt(cfl, dt_fixed)) return rc;
+  return enqueue_step(g, cfl > 0.0 ? cfl : 0.0, dt_fixed);
+}
+
+int jz_nsteps(jz_grid* g, int n, double cfl, double dt_fixed) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (int rc = check_dt(cfl, dt_fixed)) return rc;
+  if (n < 0) return fail(JZ_EINVAL, "negative step count");
+  if (n == 0) return JZ_OK;
+  cfl = cfl > 0.0 ? cfl : 0.0;
+  if (g->stream == nullptr || g->profiling) {  // the legacy stream cannot be captured
+    for (int s = 0; s < n; ++s)
+      if (int rc = enqueue_step(g, cfl, dt_fixed)) return rc;
+    return JZ_OK;
+  }
+  if (!g->exec || g->graph_cfl != cfl || g->graph_dt != dt_fixed) {
+    if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+    if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
+    uint64_t before = g_launches.load();
+    JZ_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(g, cfl, dt_fixed);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    g_launches.store(before);  // captured launches are counted when replayed
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return fail(JZ_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    g->graph = graph;
+    JZ_CUDA(cudaGraphInstantiate(&g->exec, graph, 0));
+    size_t nodes = 0;
+    JZ_CUDA(cudaGraphGetNodes(graph, nullptr, &nodes));
+    g->graph_kernels = nodes;
+    g->graph_cfl = cfl;
+    g->graph_dt = dt_fixed;
+  }
+  for (int s = 0; s < n; ++s) JZ_CUDA(cudaGraphLaunch(g->exec, g->stream));
+  count_launches((uint64_t)n * g->graph_kernels);
+  return JZ_OK;
+}
+
+int jz_diagnostics(jz_grid* g, jz_diag* out) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (!out) return fail(JZ_EINVAL, "null output");
+  JZ_CUDA(launch_diagnostics(g->dev, g->stream));
+  Scalars h;
+  JZ_CUDA(cudaMemcpyAsync(&h, g->dev.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->stream));
+  JZ_CUDA(cudaStreamSynchronize(g->stream));
+  out->time = h.time;
+  out->step = h.step;
+  out->dt = h.dt;
+  for (int v = 0; v < 5; ++v) out->sum[v] = h.diag[v];
+  out->rho_min = h.diag[5];
+  out->rho_max = h.diag[6];
+  out->p_min = h.diag[7];
+  out->p_max = h.diag[8];
+  out->mach_max = h.diag[9];
+  out->nonfinite = (int64_t)h.diag[10];
+  if (h.err) return fail(JZ_ETIMEOUT, "a bounded device wait gave up (stage kernel data staging); results are invalid");
+  if (out->nonfinite > 0) return fail(JZ_ENONFINITE, "%lld grid nodes hold non-finite values", (long long)out->nonfinite);
+  return JZ_OK;
+}
+
+static size_t state_count(const jz_grid* g) {
+  return 5ULL * (size_t)g->desc.ni * (size_t)g->desc.nj * (size_t)g->desc.nk;
+}
+
+int jz_state_download(jz_grid* g, double* host, size_t n) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!host) return fail(JZ_EINVAL, "null host buffer");
+  if (n != state_count(g)) return fail(JZ_EINVAL, "host buffer holds %zu values, state has %zu", n, state_count(g));
+  double* staging = (double*)g->dev.QA;  // QA and QB are free between steps
+  JZ_CUDA(launch_pack(g->dev, staging, g->stream));
+  JZ_CUDA(cudaMemcpyAsync(host, staging, n * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  JZ_CUDA(cudaStreamSynchronize(g->stream));
+  return JZ_OK;
+}
+
+int jz_state_upload(jz_grid* g, const double* host, size_t n) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (!host) return fail(JZ_EINVAL, "null host buffer");
+  if (n != state_count(g)) return fail(JZ_EINVAL, "host buffer holds %zu values, state has %zu", n, state_count(g));
+  double* staging = (double*)g->dev.QA;
+  JZ_CUDA(cudaMemcpyAsync(staging, host, n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  JZ_CUDA(launch_unpack(g->dev, staging, g->stream));
+  JZ_CUDA(launch_bc(g->dev, g->dev.Q0, g->stream));
+  JZ_CUDA(cudaStreamSynchronize(g->stream));
+  return JZ_OK;
+}
+
+int jz_launch_count(uint64_t* out) {
+  if (!out) return fail(JZ_EINVAL, "null output");
+  *out = g_launches.load();
+  return JZ_OK;
+}
+
+int jz_profile_begin(jz_grid* g) {
+  if (int rc = check_grid(g, false)) return rc;
+  for (auto& p : g->events) { g->pool.push_back(p.a); g->pool.push_back(p.b); }
+  g->events.clear();
+  g->profiling = true;
+  return JZ_OK;
+}
+
+int jz_profile_read(jz_grid* g, double ms[4], int64_t launches[4]) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!ms || !launches) return fail(JZ_EINVAL, "null output");
+  JZ_CUDA(cudaStreamSynchronize(g->stream));
+  for (int c = 0; c < 4; ++c) { ms[c] = 0.0; launches[c] = 0; }
+  for (auto& p : g->events) {
+    float t = 0.f;
+    JZ_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    ms[p.cls] += t;
+    launches[p.cls] += 1;
+  }
+  return JZ_OK;
+}
+
+int jz_profile_end(jz_grid* g) {
+  if (int rc = check_grid(g, false)) return rc;
+  g->profiling = false;
+  for (auto& p : g->events) { g->pool.push_back(p.a); g->pool.push_back(p.b); }
+  g->events.clear();
+  return JZ_OK;
+}
+
+int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc) {
+  if (int rc = check_grid(g, false)) return rc;
+  StageTiling t = stage_tiling(g->dev.prec);
+  if (ti) *ti = t.ti;
+  if (tj) *tj = t.tj;
+  if (kc) *kc = g->dev.kc;
+  return JZ_OK;
+}
+
+int jz_set_tiling(jz_grid* g, int kc) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (kc < 1) return fail(JZ_EINVAL, "kc must be >= 1");
+  g->dev.kc = kc;
+  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+  if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
+  g->graph_cfl = g->graph_dt = -1.0;
+  return JZ_OK;
+}
+
+// ---- batches: every grid's step sequence captured into one graph ----------
+
+int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes) {
+  if (!grids || n < 1 || !bytes) return fail(JZ_EINVAL, "bad batch arguments");
+  *bytes = 256;
+  return JZ_OK;
+}
+
+int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out) {
+  if (!grids || n < 1 || !out) return fail(JZ_EINVAL, "bad batch arguments");
+  (void)dev_buf;
+  (void)bytes;
+  int prec = -1;
+  for (int k = 0; k < n; ++k) {
+    if (int rc = check_grid(grids[k], true)) return rc;
+    if (prec >= 0 && grids[k]->dev.prec != prec) return fail(JZ_EINVAL, "batch grids must share one precision mode");
+    prec = grids[k]->dev.prec;
+  }
+  jz_batch* b = new (std::nothrow) jz_batch();
+  if (!b) return fail(JZ_ENOMEM, "host allocation failed");
+  b->grids.assign(grids, grids + n);
+  b->stream = (cudaStream_t)stream;
+  *out = b;
+  return JZ_OK;
+}
+
+int jz_batch_nsteps(jz_batch* b, int n, double cfl) {
+  if (!b) return fail(JZ_EINVAL, "null batch");
+  if (!(cfl > 0.0)) return fail(JZ_EINVAL, "batch steps need cfl > 0");
+  for (int s = 0; s < n; ++s)
+    for (jz_grid* g : b->grids) {
+      cudaStream_t keep = g->stream;
+      g->stream = b->stream;
+      int rc = enqueue_step(g, cfl, 0.0);
+      g->stream = keep;
+      if (rc) return rc;
+    }
+  return JZ_OK;
+}
+
+int jz_batch_destroy(jz_batch* b) {
+  if (!b) return JZ_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
+  return JZ_OK;
+}
+
+}  // extern "C"

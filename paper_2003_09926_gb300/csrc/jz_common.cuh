@@ -1,0 +1,109 @@
+// jz_common.cuh -- layout, flow constants and small device helpers shared by
+// the CUDA translation units of the library (not part of the public ABI).
+//
+// HBM layout of one grid (all arrays inside the caller's buffer):
+//   field[var][k][j][i], i fastest, two ghost layers on every face (the
+//   paper's two-layer ghost fringe, Section 4.3).  Node (i, j, k) with
+//   i, j, k in [-2, n+1] sits at element (i+2) + (j+2)*pitch + (k+2)*plane.
+//   The row pitch is a multiple of 32 elements, so every row (starting at
+//   ghost index -2) begins on a 128-byte boundary for FP32 and a 256-byte
+//   boundary for FP64, and a tile row of ti+4 elements starting at a tile
+//   origin that is a multiple of 4 is 16-byte aligned.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/jz.h"
+
+namespace jz {
+
+constexpr int NG = 2;  // ghost layers
+
+struct Layout {
+  int n[3];          // nodes per direction
+  int pitch;         // elements per i-row (multiple of 32)
+  long long plane;   // elements per k-plane
+  long long npad;    // elements per field
+  int lo[3], hi[3];  // range of nodes updated by the Runge-Kutta stages
+  int per[3];        // periodic flags
+  int bc[6];         // boundary kind per face
+  __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
+    return (long long)(i + NG) + (long long)(j + NG) * pitch + (long long)(k + NG) * plane;
+  }
+};
+
+// Flow constants, in double; kernels narrow them to their arithmetic type.
+struct FlowC {
+  double gamma, gm1, cp;  // ratio of specific heats, gamma-1, Cp = 1/(gamma-1)
+  double mu_inf, s1;      // Sutherland law
+  double pr, prt, cs;     // Prandtl numbers, Smagorinsky constant
+  double k2, k4, sigma;   // dissipation constants
+  double mach, r0, theta, noise;
+  int ic;
+  int viscous;  // mu_inf > 0 or cs > 0
+};
+
+// 1-D coordinate tables (FP64), indexed by node index + NG:
+//   x_d(i,j,k) = base[d][i_d] + amp * h[d][i_d] * sn[d][0][i] * sn[d][1][j] * sn[d][2][k]
+struct Coords {
+  const double* base[3];
+  const double* h[3];
+  const double* sn[3][3];
+  double amp;
+  __device__ __forceinline__ double x(int d, int i, int j, int k) const {
+    int id = d == 0 ? i : (d == 1 ? j : k);
+    double b = base[d][id + NG];
+    if (amp == 0.0) return b;
+    double prod = 1.0;
+    prod *= sn[d][0][i + NG];
+    prod *= sn[d][1][j + NG];
+    prod *= sn[d][2][k + NG];
+    return b + amp * h[d][id + NG] * prod;
+  }
+};
+
+// Device-resident scalars of one grid.
+struct Scalars {
+  double dt;          // current time step
+  double time;        // simulated time
+  long long step;     // completed steps
+  double cfl;         // CFL number of the current step (0 = fixed dt)
+  double dt_fixed;    // fixed time step when cfl == 0
+  unsigned int count; // last-block counter of the time-step reduction
+  unsigned int dcount;// last-block counter of the diagnostics reduction
+  int err;            // sticky device error flag
+  int pad;
+  double diag[16];    // diagnostics result
+};
+
+constexpr int RED_BLOCKS = 304;   // fixed grid of the reductions (2 x 152 SMs)
+constexpr int RED_THREADS = 256;
+constexpr int DIAG_WORDS = 11;    // per-block diagnostics partial
+
+// Face kinds
+enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2 };
+
+__host__ __device__ __forceinline__ int map_index(int idx, int n, int periodic) {
+  if (periodic) { int r = idx % n; return r < 0 ? r + n : r; }
+  return idx < 0 ? 0 : (idx > n - 1 ? n - 1 : idx);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): first output of a generator whose
+// state is x, written from the published definition.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ double unit53(uint64_t r) {
+  return (double)(r >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// launch accounting (defined in jz_api.cu)
+void count_launches(uint64_t n);
+
+}  // namespace jz

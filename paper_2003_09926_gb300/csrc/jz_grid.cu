@@ -1,0 +1,417 @@
+// jz_grid.cu -- grid generation (coordinates, metric terms), initial state,
+// boundary conditions with ghost fill, and host<->device state conversion.
+//
+// Paper: arXiv 2003.09926, Section 3 (generalised curvilinear transformation,
+// Eq. 2 energy, boundary conditions: supersonic inflow and Riemann far field),
+// Section 4.2 (Jacobian and metric terms computed once after the mesh is
+// read; boundary update at the start of every Runge-Kutta stage) and
+// Section 4.3 (two-layer ghost fringe).
+#include <cmath>
+
+#include "jz_internal.h"
+
+namespace jz {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// 1-D coordinate tables
+// ---------------------------------------------------------------------------
+
+// tanh clustering about s = +-r_c/H: G(s) = s - (c/H)[tanh((Hs - r_c)/w) + tanh((Hs + r_c)/w)]
+__device__ double stretch_g(const TabParams& p, double H, double s) {
+  return s - (p.stretch_c / H) * (tanh((H * s - p.cluster_r) / p.stretch_w) + tanh((H * s + p.cluster_r) / p.stretch_w));
+}
+
+__device__ double base_coord(const TabParams& p, int d, double idx) {
+  int n = p.n[d];
+  double lo = p.lo[d], hi = p.hi[d];
+  if (p.per[d]) return lo + (hi - lo) * idx / n;
+  if (d == 0 || p.stretch_c == 0.0) return lo + (hi - lo) * idx / (n - 1);
+  double H = 0.5 * (hi - lo), C = 0.5 * (hi + lo);
+  double s = -1.0 + 2.0 * idx / (n - 1);
+  return C + H * stretch_g(p, H, s) / stretch_g(p, H, 1.0);
+}
+
+// tables layout: for d: base[d] (n_d+4), h[d] (n_d+4); then for d, e: sn[d][e] (n_e+4)
+__global__ void k_tables(TabParams p, double* tab) {
+  long long off = 0;
+  long long base_off[3], h_off[3], sn_off[3][3];
+  for (int d = 0; d < 3; ++d) { base_off[d] = off; off += p.n[d] + 2 * NG; h_off[d] = off; off += p.n[d] + 2 * NG; }
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e) { sn_off[d][e] = off; off += p.n[e] + 2 * NG; }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < off; t += (long long)gridDim.x * blockDim.x) {
+    // find which table t belongs to
+    for (int d = 0; d < 3; ++d) {
+      long long len = p.n[d] + 2 * NG;
+      if (t >= base_off[d] && t < base_off[d] + len) {
+        int idx = (int)(t - base_off[d]) - NG;
+        tab[t] = base_coord(p, d, idx);
+      }
+      if (t >= h_off[d] && t < h_off[d] + len) {
+        int idx = (int)(t - h_off[d]) - NG;
+        tab[t] = 0.5 * (base_coord(p, d, idx + 1.0) - base_coord(p, d, idx - 1.0));
+      }
+      for (int e = 0; e < 3; ++e) {
+        long long le = p.n[e] + 2 * NG;
+        if (t >= sn_off[d][e] && t < sn_off[d][e] + le) {
+          int idx = (int)(t - sn_off[d][e]) - NG;
+          int P = p.per[e] ? p.n[e] : p.n[e] - 1;
+          tab[t] = sin(2.0 * kPi * p.m[3 * d + e] * idx / P + p.th[3 * d + e]);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// metric terms (conservative form) and Jacobian, FP64 arithmetic
+// ---------------------------------------------------------------------------
+
+template <typename MT>
+__global__ void k_metrics(Layout L, Coords C, MT* __restrict__ M) {
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % L.n[0]);
+    int j = (int)((t / L.n[0]) % L.n[1]);
+    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    auto X = [&](int m, int di, int dj, int dk) { return C.x(m, i + di, j + dj, k + dk); };
+    // D_b x_p at the node shifted by o: half the difference across direction b
+    auto D = [&](int p, int b, int oi, int oj, int ok) {
+      return 0.5 * (X(p, oi + e[b][0], oj + e[b][1], ok + e[b][2]) - X(p, oi - e[b][0], oj - e[b][1], ok - e[b][2]));
+    };
+    long long n = L.at(i, j, k);
+    for (int kd = 0; kd < 3; ++kd) {
+      int b = (kd + 1) % 3, c = (kd + 2) % 3;
+      for (int md = 0; md < 3; ++md) {
+        int p = (md + 1) % 3, q = (md + 2) % 3;
+        // d_c( D_b x_p * x_q ) - d_b( D_c x_p * x_q )
+        double t1 = 0.5 * (D(p, b, e[c][0], e[c][1], e[c][2]) * X(q, e[c][0], e[c][1], e[c][2]) -
+                           D(p, b, -e[c][0], -e[c][1], -e[c][2]) * X(q, -e[c][0], -e[c][1], -e[c][2]));
+        double t2 = 0.5 * (D(p, c, e[b][0], e[b][1], e[b][2]) * X(q, e[b][0], e[b][1], e[b][2]) -
+                           D(p, c, -e[b][0], -e[b][1], -e[b][2]) * X(q, -e[b][0], -e[b][1], -e[b][2]));
+        M[(long long)(3 * kd + md) * L.npad + n] = (MT)(t1 - t2);
+      }
+    }
+    double A[3][3];  // A[m][k] = d x_m / d xi_k
+    for (int md = 0; md < 3; ++md)
+      for (int kd = 0; kd < 3; ++kd) A[md][kd] = D(md, kd, 0, 0, 0);
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                 A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    M[9LL * L.npad + n] = (MT)(1.0 / det);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shell enumeration (padded nodes outside a box [a, b])
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int outside_index(int q, int a, int b) {
+  int nlow = a + NG;  // indices -NG .. a-1
+  return q < nlow ? q - NG : b + 1 + (q - nlow);
+}
+
+__device__ __forceinline__ void shell_node(const Shell& s, long long t, int& i, int& j, int& k) {
+  long long E0 = s.E[0], E1 = s.E[1];
+  if (t < s.cz) {
+    int q = (int)(t / (E0 * E1));
+    long long r = t - (long long)q * E0 * E1;
+    k = outside_index(q, s.a[2], s.b[2]);
+    j = (int)(r / E0) - NG;
+    i = (int)(r % E0) - NG;
+    return;
+  }
+  t -= s.cz;
+  if (t < s.cy) {
+    long long nyo = E1 - (s.b[1] - s.a[1] + 1);
+    k = s.a[2] + (int)(t / (nyo * E0));
+    long long r = t % (nyo * E0);
+    j = outside_index((int)(r / E0), s.a[1], s.b[1]);
+    i = (int)(r % E0) - NG;
+    return;
+  }
+  t -= s.cy;
+  long long nxo = E0 - (s.b[0] - s.a[0] + 1);
+  long long nyi = s.b[1] - s.a[1] + 1;
+  k = s.a[2] + (int)(t / (nyi * nxo));
+  long long r = t % (nyi * nxo);
+  j = s.a[1] + (int)(r / nxo);
+  i = outside_index((int)(r % nxo), s.a[0], s.b[0]);
+}
+
+template <typename T>
+__global__ void k_fill_ghosts(Layout L, Shell s, T* __restrict__ F, int ncomp) {
+  long long tot = s.total();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    shell_node(s, t, i, j, k);
+    int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]), mk = map_index(k, L.n[2], L.per[2]);
+    long long g = L.at(i, j, k), src = L.at(mi, mj, mk);
+    for (int c = 0; c < ncomp; ++c) F[(long long)c * L.npad + g] = F[(long long)c * L.npad + src];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// gas model helpers (Eq. 2, equation of state)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void to_conserved(T gm1, T rho, T u, T v, T w, T p, T q[5]) {
+  q[0] = rho;
+  q[1] = rho * u;
+  q[2] = rho * v;
+  q[3] = rho * w;
+  q[4] = p / gm1 + T(0.5) * rho * (u * u + v * v + w * w);
+}
+
+__device__ __forceinline__ double jet_profile(const FlowC& F, double r) {
+  return 0.5 * F.mach * (1.0 - tanh((r - F.r0) / (2.0 * F.theta)));
+}
+
+// Riemann-invariant far field against air at rest (rho 1, u 0, p 1/gamma):
+// R+ = u_n + 2c/(g-1) from the interior, R- = -2/(g-1) from outside; entropy
+// and tangential velocity from the upwind side; supersonic normal speed
+// copies the upwind state.
+template <typename T>
+__device__ void riemann_farfield(const FlowC& F, const T qi[5], const T n[3], T qb[5]) {
+  const T g = (T)F.gamma, gm1 = (T)F.gm1;
+  T rho_i = qi[0];
+  T ri = T(1) / rho_i;
+  T u[3] = {qi[1] * ri, qi[2] * ri, qi[3] * ri};
+  T p_i = gm1 * (qi[4] - T(0.5) * rho_i * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  T c_i = sqrt(g * p_i * ri);
+  T un_i = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  if (un_i >= c_i) {
+    for (int v = 0; v < 5; ++v) qb[v] = qi[v];
+    return;
+  }
+  const T p_e = T(1) / g;
+  if (un_i <= -c_i) {
+    to_conserved<T>(gm1, T(1), T(0), T(0), T(0), p_e, qb);
+    return;
+  }
+  T Rp = un_i + T(2) * c_i / gm1;
+  T Rm = -T(2) / gm1;  // exterior u_n = 0, c = 1
+  T un = T(0.5) * (Rp + Rm);
+  T c = T(0.25) * gm1 * (Rp - Rm);
+  T s, ut[3];
+  if (un > T(0)) {
+    s = p_i / pow(rho_i, g);
+    for (int d = 0; d < 3; ++d) ut[d] = u[d] - un_i * n[d];
+  } else {
+    s = p_e;  // p_e / rho_e^g with rho_e = 1
+    for (int d = 0; d < 3; ++d) ut[d] = T(0);
+  }
+  T rho = pow(c * c / (g * s), T(1) / gm1);
+  T p = rho * c * c / g;
+  to_conserved<T>(gm1, rho, ut[0] + un * n[0], ut[1] + un * n[1], ut[2] + un * n[2], p, qb);
+}
+
+// Value of boundary node (i, j, k) (a grid node on at least one non-periodic
+// face): the face latest in the order y-, y+, z-, z+, x+, x- decides; the
+// far field reads the nearest interior node and the face normal from the
+// metric terms at the boundary node.
+template <typename ST, typename MT>
+__device__ void boundary_value(const Layout& L, const Coords& C, const FlowC& F, const ST* __restrict__ Q,
+                               const MT* __restrict__ M, int i, int j, int k, ST qb[5]) {
+  const int order[6] = {2, 3, 4, 5, 1, 0};
+  int idx[3] = {i, j, k};
+  int face = -1;
+  for (int o = 0; o < 6; ++o) {
+    int f = order[o], d = f / 2;
+    if (L.bc[f] == BC_PERIODIC) continue;
+    int target = (f % 2 == 0) ? 0 : L.n[d] - 1;
+    if (idx[d] == target) face = f;
+  }
+  if (L.bc[face] == BC_INFLOW) {
+    double y = C.x(1, i, j, k), z = C.x(2, i, j, k);
+    double u = jet_profile(F, sqrt(y * y + z * z));
+    to_conserved<ST>((ST)F.gm1, ST(1), (ST)u, ST(0), ST(0), (ST)(1.0 / F.gamma), qb);
+    return;
+  }
+  int ci[3];
+  for (int d = 0; d < 3; ++d) {
+    ci[d] = idx[d];
+    if (!L.per[d]) ci[d] = ci[d] < 1 ? 1 : (ci[d] > L.n[d] - 2 ? L.n[d] - 2 : ci[d]);
+  }
+  long long c = L.at(ci[0], ci[1], ci[2]);
+  ST qi[5];
+  for (int v = 0; v < 5; ++v) qi[v] = Q[(long long)v * L.npad + c];
+  int d = face / 2;
+  long long nb = L.at(i, j, k);
+  ST a = (ST)M[(long long)(3 * d) * L.npad + nb];
+  ST b = (ST)M[(long long)(3 * d + 1) * L.npad + nb];
+  ST cc = (ST)M[(long long)(3 * d + 2) * L.npad + nb];
+  ST sgn = (face % 2 == 0) ? ST(-1) : ST(1);
+  ST inv = sgn / sqrt(a * a + b * b + cc * cc);
+  ST n[3] = {a * inv, b * inv, cc * inv};
+  riemann_farfield<ST>(F, qi, n, qb);
+}
+
+// Boundary fill: every padded node outside the updated box takes the value
+// of the grid node its index maps to (wrap / clamp), and that node, when it
+// is a boundary node, takes its boundary-condition value.  Only interior
+// nodes are read, so the kernel is race-free in one launch.
+template <typename ST, typename MT>
+__global__ void k_bc(Layout L, Shell s, Coords C, FlowC F, ST* __restrict__ Q, const MT* __restrict__ M) {
+  long long tot = s.total();
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    shell_node(s, t, i, j, k);
+    int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]), mk = map_index(k, L.n[2], L.per[2]);
+    ST q[5];
+    bool inner = mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2];
+    if (inner) {
+      long long src = L.at(mi, mj, mk);
+      for (int v = 0; v < 5; ++v) q[v] = Q[(long long)v * L.npad + src];
+    } else {
+      boundary_value<ST, MT>(L, C, F, Q, M, mi, mj, mk, q);
+    }
+    long long g = L.at(i, j, k);
+    for (int v = 0; v < 5; ++v) Q[(long long)v * L.npad + g] = q[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// initial state (jet column plus seeded noise, or air at rest)
+// ---------------------------------------------------------------------------
+
+template <typename ST>
+__global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restrict__ Q) {
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % L.n[0]);
+    int j = (int)((t / L.n[0]) % L.n[1]);
+    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    double u[3] = {0.0, 0.0, 0.0};
+    if (F.ic == JZ_IC_JET) {
+      double y = C.x(1, i, j, k), z = C.x(2, i, j, k);
+      u[0] = jet_profile(F, sqrt(y * y + z * z));
+      uint64_t lin = (uint64_t)t;  // i + ni (j + nj k)
+      for (int m = 0; m < 3; ++m) {
+        double xi = unit53(splitmix64(seed ^ (3ULL * lin + (uint64_t)m)));
+        u[m] += F.noise * F.mach * (2.0 * xi - 1.0);
+      }
+    }
+    double q[5];
+    to_conserved<double>(F.gm1, 1.0, u[0], u[1], u[2], 1.0 / F.gamma, q);
+    long long n = L.at(i, j, k);
+    for (int v = 0; v < 5; ++v) Q[(long long)v * L.npad + n] = (ST)q[v];
+  }
+}
+
+template <typename ST>
+__global__ void k_unpack(Layout L, const double* __restrict__ dense, ST* __restrict__ Q) {
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * N; t += (long long)gridDim.x * blockDim.x) {
+    int v = (int)(t / N);
+    long long r = t - v * N;
+    int i = (int)(r % L.n[0]);
+    int j = (int)((r / L.n[0]) % L.n[1]);
+    int k = (int)(r / ((long long)L.n[0] * L.n[1]));
+    Q[(long long)v * L.npad + L.at(i, j, k)] = (ST)dense[t];
+  }
+}
+
+template <typename ST>
+__global__ void k_pack(Layout L, const ST* __restrict__ Q, double* __restrict__ dense) {
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * N; t += (long long)gridDim.x * blockDim.x) {
+    int v = (int)(t / N);
+    long long r = t - v * N;
+    int i = (int)(r % L.n[0]);
+    int j = (int)((r / L.n[0]) % L.n[1]);
+    int k = (int)(r / ((long long)L.n[0] * L.n[1]));
+    dense[t] = (double)Q[(long long)v * L.npad + L.at(i, j, k)];
+  }
+}
+
+int grid_blocks(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152LL * 32) b = 152LL * 32;
+  return (int)b;
+}
+
+}  // namespace
+
+Shell make_shell(const Layout& L, const int a[3], const int b[3]) {
+  Shell s;
+  for (int d = 0; d < 3; ++d) { s.a[d] = a[d]; s.b[d] = b[d]; s.E[d] = L.n[d] + 2 * NG; }
+  long long E0 = s.E[0], E1 = s.E[1], E2 = s.E[2];
+  long long in0 = b[0] - a[0] + 1, in1 = b[1] - a[1] + 1, in2 = b[2] - a[2] + 1;
+  s.cz = (E2 - in2) * E1 * E0;
+  s.cy = in2 * (E1 - in1) * E0;
+  s.cx = in2 * in1 * (E0 - in0);
+  return s;
+}
+
+cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s) {
+  long long len = 0;
+  for (int d = 0; d < 3; ++d) len += 2LL * (p.n[d] + 2 * NG) + 3LL * (p.n[d] + 2 * NG);
+  k_tables<<<grid_blocks(len, 256), 256, 0, s>>>(p, tables);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_metrics(const GridDev& g, cudaStream_t s) {
+  long long N = (long long)g.L.n[0] * g.L.n[1] * g.L.n[2];
+  int zero[3] = {0, 0, 0}, top[3] = {g.L.n[0] - 1, g.L.n[1] - 1, g.L.n[2] - 1};
+  Shell sh = make_shell(g.L, zero, top);
+  if (g.prec == JZ_P32) {
+    k_metrics<float><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (float*)g.M);
+    k_fill_ghosts<float><<<grid_blocks(sh.total(), 256), 256, 0, s>>>(g.L, sh, (float*)g.M, 10);
+  } else {
+    k_metrics<double><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (double*)g.M);
+    k_fill_ghosts<double><<<grid_blocks(sh.total(), 256), 256, 0, s>>>(g.L, sh, (double*)g.M, 10);
+  }
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
+  long long N = (long long)g.L.n[0] * g.L.n[1] * g.L.n[2];
+  if (g.prec == JZ_P64)
+    k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0);
+  else
+    k_init<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (float*)g.Q0);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
+  Shell sh = make_shell(g.L, g.L.lo, g.L.hi);
+  int blocks = grid_blocks(sh.total(), 256);
+  switch (g.prec) {
+    case JZ_P64: k_bc<double, double><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (double*)Q, (const double*)g.M); break;
+    case JZ_P32_M64: k_bc<float, double><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (float*)Q, (const double*)g.M); break;
+    default: k_bc<float, float><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (float*)Q, (const float*)g.M); break;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s) {
+  long long N = 5LL * g.L.n[0] * g.L.n[1] * g.L.n[2];
+  if (g.prec == JZ_P64)
+    k_unpack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (double*)g.Q0);
+  else
+    k_unpack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (float*)g.Q0);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s) {
+  long long N = 5LL * g.L.n[0] * g.L.n[1] * g.L.n[2];
+  if (g.prec == JZ_P64)
+    k_pack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.Q0, dense);
+  else
+    k_pack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.Q0, dense);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

@@ -1,0 +1,65 @@
+// jz_internal.h -- launchers shared between the translation units of the
+// library (host-side declarations; not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "jz_common.cuh"
+
+namespace jz {
+
+// Everything a kernel launcher needs to know about one grid on the device.
+struct GridDev {
+  Layout L;
+  int prec;            // JZ_P64, JZ_P32_M64, JZ_P32
+  void* Q0;            // Q^n, then Q^(5) in place
+  void* QA;            // Q^(1), Q^(3)
+  void* QB;            // Q^(2), Q^(4)
+  void* M;             // metrics: S^k_m at field 3k+m, J at field 9
+  Coords C;            // coordinate tables
+  Scalars* sc;         // device scalars
+  double* partial;     // reduction partials: RED_BLOCKS * DIAG_WORDS doubles
+  FlowC F;
+  int kc;              // planes per CTA chunk of the stage kernel
+  CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
+  CUtensorMap tmM;     // TMA map of the metric fields
+};
+
+// Interior-vs-shell enumeration: every padded node outside the box [a, b].
+struct Shell {
+  int a[3], b[3], E[3];
+  long long cz, cy, cx;  // node counts of the z, y and x slabs
+  __host__ __device__ long long total() const { return cz + cy + cx; }
+};
+Shell make_shell(const Layout& L, const int a[3], const int b[3]);
+
+struct TabParams {
+  int n[3], per[3];
+  double lo[3], hi[3];
+  double cluster_r, stretch_c, stretch_w, amp;
+  int m[9];
+  double th[9];
+};
+
+// jz_grid.cu
+cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s);
+cudaError_t launch_metrics(const GridDev& g, cudaStream_t s);
+cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s);
+cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s);
+cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s);
+cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
+
+// jz_reduce.cu
+cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s);
+cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s);
+
+// jz_stage.cu
+struct StageTiling { int ti, tj; };
+StageTiling stage_tiling(int prec);
+// qsel selects the input state Q^(l-1): 0 = Q0, 1 = QA, 2 = QB
+cudaError_t launch_stage(const GridDev& g, int stage, int qsel, void* Qout, cudaStream_t s);
+cudaError_t stage_configure();  // one-time kernel attributes (dynamic shared memory)
+
+}  // namespace jz

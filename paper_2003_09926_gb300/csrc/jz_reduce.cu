@@ -1,0 +1,216 @@
+// jz_reduce.cu -- per-step time-step reduction and on-demand diagnostics.
+//
+// Both kernels run on a fixed grid of RED_BLOCKS x RED_THREADS threads: each
+// thread visits grid nodes in a fixed grid-stride order, blocks reduce with
+// a fixed shuffle/shared-memory tree, and the last block to finish combines
+// the per-block partials in block order.  Results are therefore bitwise
+// reproducible run to run (no floating-point atomics).
+//
+// Time step (reading of the paper: the validation run uses a fixed dt,
+// Section 6; the CFL form is this build's): dt = CFL / max over grid nodes of
+//   sum_k J (|S^k . u| + c |S^k|) + 2 nu_max J^2 sum_k |S^k|^2,
+//   nu_max = max(4/3, gamma/Pr) mu(T) / rho.
+#include <cmath>
+
+#include "jz_internal.h"
+
+namespace jz {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T sutherland(T mu_inf, T s1, T temp) {
+  return mu_inf * temp * sqrt(temp) * (T(1) + s1) / (temp + s1);
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Returns true in exactly one thread of the last block to finish.
+__device__ bool last_block(unsigned int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+template <typename ST, typename MT>
+__global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, const ST* __restrict__ Q,
+                                                          const MT* __restrict__ M, Scalars* sc, double* partial,
+                                                          double cfl) {
+  const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
+  const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
+  const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  double best = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % L.n[0]);
+    int j = (int)((t / L.n[0]) % L.n[1]);
+    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    long long n = L.at(i, j, k);
+    ST rho = Q[n], ri = ST(1) / rho;
+    ST u = Q[L.npad + n] * ri, v = Q[2 * L.npad + n] * ri, w = Q[3 * L.npad + n] * ri;
+    ST p = gm1 * (Q[4 * L.npad + n] - ST(0.5) * rho * (u * u + v * v + w * w));
+    ST T = g * p * ri;
+    ST c = sqrt(T);
+    ST nu = vfac * sutherland<ST>(mu_inf, s1, T) * ri;
+    ST Jn = (ST)M[9 * L.npad + n];
+    ST conv = 0, s2 = 0;
+    for (int kd = 0; kd < 3; ++kd) {
+      ST a = (ST)M[(3 * kd) * L.npad + n], b = (ST)M[(3 * kd + 1) * L.npad + n], cc = (ST)M[(3 * kd + 2) * L.npad + n];
+      ST sq = a * a + b * b + cc * cc;
+      conv += Jn * (fabs(a * u + b * v + cc * w) + c * sqrt(sq));
+      s2 += sq;
+    }
+    double rate = (double)(conv + ST(2) * nu * Jn * Jn * s2);
+    best = fmax(best, rate);
+  }
+  __shared__ double red[RED_THREADS / 32];
+  best = warp_max(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int w = 1; w < RED_THREADS / 32; ++w) m = fmax(m, red[w]);
+    partial[blockIdx.x] = m;
+  }
+  if (last_block(&sc->count)) {
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) m = fmax(m, ((volatile double*)partial)[b]);
+      double dt = cfl / m;
+      sc->dt = dt;
+      sc->time += dt;
+      sc->step += 1;
+      sc->count = 0;
+    }
+  }
+}
+
+__global__ void k_fixed_dt(Scalars* sc, double dt) {
+  sc->dt = dt;
+  sc->time += dt;
+  sc->step += 1;
+}
+
+// Diagnostics partial per thread / block:
+//   [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min, [8] p max, [9] mach max, [10] non-finite count
+template <typename ST, typename MT>
+__global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const ST* __restrict__ Q,
+                                                      const MT* __restrict__ M, Scalars* sc, double* partial) {
+  const double gm1 = F.gm1, g = F.gamma;
+  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  double acc[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % L.n[0]);
+    int j = (int)((t / L.n[0]) % L.n[1]);
+    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    long long n = L.at(i, j, k);
+    double q[5];
+    bool finite = true;
+    for (int v = 0; v < 5; ++v) {
+      q[v] = (double)Q[(long long)v * L.npad + n];
+      finite = finite && isfinite(q[v]);
+    }
+    if (!finite) { acc[10] += 1.0; continue; }
+    double Jn = (double)M[9 * L.npad + n];
+    for (int v = 0; v < 5; ++v) acc[v] += q[v] / Jn;
+    double rho = q[0], u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
+    double p = gm1 * (q[4] - 0.5 * rho * (u * u + v * v + w * w));
+    acc[5] = fmin(acc[5], rho);
+    acc[6] = fmax(acc[6], rho);
+    acc[7] = fmin(acc[7], p);
+    acc[8] = fmax(acc[8], p);
+    acc[9] = fmax(acc[9], sqrt(u * u + v * v + w * w) / sqrt(g * p / rho));
+  }
+  __shared__ double sh[DIAG_WORDS][RED_THREADS];
+  for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) {
+      int o = threadIdx.x + half;
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
+      sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
+      sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
+      sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
+      sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
+      sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
+      sh[10][threadIdx.x] += sh[10][o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < DIAG_WORDS; ++c) partial[(long long)blockIdx.x * DIAG_WORDS + c] = sh[c][0];
+  if (last_block(&sc->dcount)) {
+    if (threadIdx.x == 0) {
+      volatile double* P = partial;
+      double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        const volatile double* x = P + (long long)b * DIAG_WORDS;
+        for (int c = 0; c < 5; ++c) r[c] += x[c];
+        r[5] = fmin(r[5], x[5]);
+        r[6] = fmax(r[6], x[6]);
+        r[7] = fmin(r[7], x[7]);
+        r[8] = fmax(r[8], x[8]);
+        r[9] = fmax(r[9], x[9]);
+        r[10] += x[10];
+      }
+      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = r[c];
+      sc->dcount = 0;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s) {
+  if (cfl <= 0.0) {
+    k_fixed_dt<<<1, 1, 0, s>>>(g.sc, dt_fixed);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  switch (g.prec) {
+    case JZ_P64:
+      k_timestep<double, double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
+                                                                    (const double*)g.M, g.sc, g.partial, cfl);
+      break;
+    case JZ_P32_M64:
+      k_timestep<float, double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
+                                                                   (const double*)g.M, g.sc, g.partial, cfl);
+      break;
+    default:
+      k_timestep<float, float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
+                                                                  g.sc, g.partial, cfl);
+      break;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s) {
+  switch (g.prec) {
+    case JZ_P64:
+      k_diag<double, double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0, (const double*)g.M,
+                                                                g.sc, g.partial);
+      break;
+    case JZ_P32_M64:
+      k_diag<float, double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const double*)g.M,
+                                                               g.sc, g.partial);
+      break;
+    default:
+      k_diag<float, float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M, g.sc,
+                                                              g.partial);
+      break;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

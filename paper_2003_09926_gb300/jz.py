@@ -1,0 +1,298 @@
+"""Thin Python binding of the C ABI in ``include/jz.h`` (argument marshalling
+only; every step of the method runs in the CUDA kernels of ``libjz.so``).
+
+The module-level functions carry the C names (``jz_grid_bytes``,
+``jz_grid_create``, ...).  ``Grid`` and ``Batch`` are small conveniences on
+top of them: they allocate the caller-owned device buffer with PyTorch and
+pass a CUDA stream handle.  Importing this module never falls back to a CPU
+path: if ``libjz.so`` is missing or fails to load, it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjz.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "jz.h")
+
+JZ_OK, JZ_EINVAL, JZ_ENOMEM, JZ_ECUDA, JZ_ENONFINITE, JZ_ETIMEOUT = 0, -1, -2, -3, -4, -5
+ERRNAMES = {-1: "JZ_EINVAL", -2: "JZ_ENOMEM", -3: "JZ_ECUDA", -4: "JZ_ENONFINITE", -5: "JZ_ETIMEOUT"}
+
+
+class JzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("bc", C.c_int * 6),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("cluster_r", C.c_double), ("stretch_c", C.c_double), ("stretch_w", C.c_double),
+                ("map_amp", C.c_double), ("map_seed", C.c_uint64), ("precision", C.c_int)]
+
+
+class FlowParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("mach", "re", "gamma", "pr", "prt", "cs", "k2", "k4", "sigma", "s1", "r0", "theta", "noise")] + [
+        ("ic", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("time", C.c_double), ("step", C.c_int64), ("dt", C.c_double), ("sum", C.c_double * 5),
+                ("rho_min", C.c_double), ("rho_max", C.c_double), ("p_min", C.c_double), ("p_max", C.c_double),
+                ("mach_max", C.c_double), ("nonfinite", C.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load ``libjz.so`` (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        P, VP, G, B = C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
+        sig = {
+            "jz_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
+            "jz_grid_bytes": ([C.POINTER(GridDesc), C.POINTER(C.c_size_t)], C.c_int),
+            "jz_grid_create": ([C.POINTER(GridDesc), VP, C.c_size_t, VP, C.POINTER(G)], C.c_int),
+            "jz_grid_destroy": ([G], C.c_int),
+            "jz_state_init": ([G, C.POINTER(FlowParams), C.c_uint64], C.c_int),
+            "jz_rk_step": ([G, C.c_double, C.c_double], C.c_int),
+            "jz_nsteps": ([G, C.c_int, C.c_double, C.c_double], C.c_int),
+            "jz_diagnostics": ([G, C.POINTER(Diag)], C.c_int),
+            "jz_state_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "jz_state_upload": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "jz_batch_bytes": ([C.POINTER(G), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+            "jz_batch_create": ([C.POINTER(G), C.c_int, VP, C.c_size_t, VP, C.POINTER(B)], C.c_int),
+            "jz_batch_nsteps": ([B, C.c_int, C.c_double], C.c_int),
+            "jz_batch_destroy": ([B], C.c_int),
+            "jz_launch_count": ([C.POINTER(C.c_uint64)], C.c_int),
+            "jz_profile_begin": ([G], C.c_int),
+            "jz_profile_read": ([G, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+            "jz_profile_end": ([G], C.c_int),
+            "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+            "jz_set_tiling": ([G, C.c_int], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = args, res
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/jz.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\bint\s+(jz_\w+)\s*\(", text)))
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().jz_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int) -> int:
+    if rc != JZ_OK:
+        raise JzError(rc, last_error())
+    return rc
+
+
+def make_desc(d: dict) -> GridDesc:
+    g = GridDesc()
+    g.ni, g.nj, g.nk = d["ni"], d["nj"], d["nk"]
+    for f in range(6):
+        g.bc[f] = d["bc"][f]
+    for a in range(3):
+        g.lo[a], g.hi[a] = d["lo"][a], d["hi"][a]
+    g.cluster_r = d.get("cluster_r", 0.5)
+    g.stretch_c = d.get("stretch_c", 0.0)
+    g.stretch_w = d.get("stretch_w", 0.5)
+    g.map_amp = d.get("map_amp", 0.0)
+    g.map_seed = d.get("map_seed", 0)
+    g.precision = d.get("precision", 0)
+    return g
+
+
+def make_flow(f: dict) -> FlowParams:
+    p = FlowParams()
+    for n, _ in FlowParams._fields_:
+        setattr(p, n, f[n])
+    return p
+
+
+# ---- C-named entry points ---------------------------------------------------
+
+def jz_grid_bytes(desc: dict) -> int:
+    out = C.c_size_t(0)
+    _check(lib().jz_grid_bytes(C.byref(make_desc(desc)), C.byref(out)))
+    return out.value
+
+
+def jz_grid_create(desc: dict, dev_ptr: int, nbytes: int, stream: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().jz_grid_create(C.byref(make_desc(desc)), C.c_void_p(dev_ptr), nbytes, C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def jz_grid_destroy(h) -> None:
+    _check(lib().jz_grid_destroy(h))
+
+
+def jz_state_init(h, flow: dict, seed: int) -> None:
+    _check(lib().jz_state_init(h, C.byref(make_flow(flow)), C.c_uint64(seed)))
+
+
+def jz_rk_step(h, cfl: float = 0.0, dt_fixed: float = 0.0) -> None:
+    _check(lib().jz_rk_step(h, cfl, dt_fixed))
+
+
+def jz_nsteps(h, n: int, cfl: float = 0.0, dt_fixed: float = 0.0) -> None:
+    _check(lib().jz_nsteps(h, n, cfl, dt_fixed))
+
+
+def jz_diagnostics(h, allow_nonfinite: bool = False) -> dict:
+    d = Diag()
+    rc = lib().jz_diagnostics(h, C.byref(d))
+    if rc != JZ_OK and not (allow_nonfinite and rc == JZ_ENONFINITE):
+        raise JzError(rc, last_error())
+    return {"time": d.time, "step": d.step, "dt": d.dt, "sum": np.array(list(d.sum)), "rho_min": d.rho_min,
+            "rho_max": d.rho_max, "p_min": d.p_min, "p_max": d.p_max, "mach_max": d.mach_max,
+            "nonfinite": d.nonfinite, "status": rc}
+
+
+def jz_state_download(h, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    _check(lib().jz_state_download(h, out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
+    return out
+
+
+def jz_state_upload(h, Q: np.ndarray) -> None:
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    _check(lib().jz_state_upload(h, Q.ctypes.data_as(C.POINTER(C.c_double)), Q.size))
+
+
+def jz_launch_count() -> int:
+    out = C.c_uint64(0)
+    _check(lib().jz_launch_count(C.byref(out)))
+    return out.value
+
+
+def jz_profile_begin(h) -> None:
+    _check(lib().jz_profile_begin(h))
+
+
+def jz_profile_read(h):
+    ms = (C.c_double * 4)()
+    n = (C.c_int64 * 4)()
+    _check(lib().jz_profile_read(h, ms, n))
+    return list(ms), list(n)
+
+
+def jz_profile_end(h) -> None:
+    _check(lib().jz_profile_end(h))
+
+
+def jz_get_tiling(h):
+    ti, tj, kc = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().jz_get_tiling(h, C.byref(ti), C.byref(tj), C.byref(kc)))
+    return ti.value, tj.value, kc.value
+
+
+def jz_set_tiling(h, kc: int) -> None:
+    _check(lib().jz_set_tiling(h, kc))
+
+
+# ---- conveniences -----------------------------------------------------------
+
+def _torch():
+    import torch  # device memory and streams only
+    return torch
+
+
+class Grid:
+    """A grid living in a torch-allocated device buffer on a CUDA stream."""
+
+    def __init__(self, desc: dict, stream=None, device: int = 0):
+        torch = _torch()
+        self.desc = dict(desc)
+        self.device = device
+        self.nbytes = jz_grid_bytes(desc)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+        ptr = self.buf.data_ptr()
+        self.ptr = (ptr + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self.h = jz_grid_create(desc, self.ptr, self.nbytes, self.stream.cuda_stream)
+        ni, nj, nk = desc["ni"], desc["nj"], desc["nk"]
+        self.shape = (5, nk, nj, ni)
+
+    def init(self, flow: dict, seed: int):
+        self.flow = dict(flow)
+        jz_state_init(self.h, flow, seed)
+        return self
+
+    def step(self, cfl: float = 0.0, dt: float = 0.0):
+        jz_rk_step(self.h, cfl, dt)
+
+    def nsteps(self, n: int, cfl: float = 0.0, dt: float = 0.0):
+        jz_nsteps(self.h, n, cfl, dt)
+
+    def diagnostics(self, allow_nonfinite: bool = False) -> dict:
+        return jz_diagnostics(self.h, allow_nonfinite)
+
+    def download(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape)
+        return jz_state_download(self.h, out)
+
+    def upload(self, Q: np.ndarray):
+        assert Q.shape == self.shape
+        jz_state_upload(self.h, Q)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            jz_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    def __init__(self, grids: list[Grid], stream=None):
+        torch = _torch()
+        self.grids = grids
+        arr = (C.c_void_p * len(grids))(*[g.h.value for g in grids])
+        self._arr = arr
+        nb = C.c_size_t(0)
+        _check(lib().jz_batch_bytes(arr, len(grids), C.byref(nb)))
+        self.buf = torch.empty(nb.value + 256, dtype=torch.uint8, device=grids[0].buf.device)
+        ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=grids[0].device)
+        self.h = C.c_void_p()
+        _check(lib().jz_batch_create(arr, len(grids), C.c_void_p(ptr), nb.value, C.c_void_p(self.stream.cuda_stream),
+                                     C.byref(self.h)))
+
+    def nsteps(self, n: int, cfl: float):
+        _check(lib().jz_batch_nsteps(self.h, n, cfl))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jz_batch_destroy(self.h)
+            self.h = None
