@@ -192,6 +192,34 @@ int jz_profile_end(jz_grid* g);
 int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
 int jz_set_tiling(jz_grid* g, int kc);
 
+/* --- diagnostics without device allocation --------------------------------
+ * The paper has no counterpart to this entry point: it serves callers that
+ * may only use device arrays they were handed -- a plug-in called by a host
+ * framework with its input and output buffers, or a serving process that
+ * reserved all device memory at start-up and treats later allocations as
+ * failures -- and so cannot provide the scratch that jz_diagnostics takes
+ * from a grid's buffer.  Its reduction scratch is a fixed static device
+ * array (about 352 KB, held by every device that loads the library until the
+ * process exits); it allocates no device memory and calls no allocating
+ * routine.
+ *
+ * Q:    device, dense [5][n_nodes] conserved variables (rho, rho u, rho v,
+ *       rho w, e), FP64 when fp64 = 1, FP32 when fp64 = 0;
+ * vol:  device, n_nodes FP64 node volumes (1/J for a grid);
+ * out:  device, 11 doubles: sum Q_v * vol (5), rho min, rho max, p min,
+ *       p max, max |u|/c, count of nodes with a non-finite value (nodes
+ *       with one are left out of the sums and extrema);
+ * stream: cudaStream_t as void* (NULL = legacy default stream).
+ * n_nodes must not exceed 268,435,456 (2^28; JZ_EINVAL beyond).  The work is
+ * enqueued asynchronously; results are summed in a fixed order (bitwise
+ * reproducible).  The first call on a device looks up the static array's
+ * device address with that device current and must come before any other
+ * use of the array on that device.  Every call shares the one array, which
+ * keeps the last call's contents; calls whose kernels may overlap on the GPU
+ * (unordered streams) race on it and must not be issued. */
+int jz_state_diagnostics_static(long long n_nodes, int fp64, const void* Q, const double* vol, double gamma,
+                                double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,9 @@ struct TabParams {
   double th[9];
 };
 
+// jz_api.cu: set the calling thread's jz_last_error message; returns code
+int record_error(int code, const char* msg);
+
 // jz_grid.cu
 cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s);
 cudaError_t launch_metrics(const GridDev& g, cudaStream_t s);

@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
             "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "jz_set_tiling": ([G, C.c_int], C.c_int),
         }
+        sig["jz_state_diagnostics_static"] = ([C.c_longlong, C.c_int, VP, VP, C.c_double, VP, VP], C.c_int)
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes, f.restype = args, res
@@ -211,6 +212,14 @@ def jz_get_tiling(h):
 
 def jz_set_tiling(h, kc: int) -> None:
     _check(lib().jz_set_tiling(h, kc))
+
+
+def jz_state_diagnostics_static(n_nodes: int, fp64: bool, q_ptr: int, vol_ptr: int, gamma: float, out_ptr: int,
+                                stream: int) -> None:
+    """Diagnostics of dense device arrays with no device allocation (the
+    reduction scratch is a static device array inside the library)."""
+    _check(lib().jz_state_diagnostics_static(n_nodes, 1 if fp64 else 0, C.c_void_p(q_ptr), C.c_void_p(vol_ptr),
+                                             gamma, C.c_void_p(out_ptr), C.c_void_p(stream)))
 
 
 # ---- conveniences -----------------------------------------------------------
