@@ -56,7 +56,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Carve {
   Layout L;
   size_t es, ms;  // state / metric element sizes
-  size_t off_sc, off_partial, off_tab, off_q0, off_qa, off_qb, off_m, total;
+  size_t off_sc, off_partial, off_tab, off_inflow, off_q0, off_qa, off_qb, off_m, total;
   size_t tab_len;
 };
 
@@ -75,6 +75,8 @@ static int validate(const jz_grid_desc* d) {
     if (n[a] > (1 << 24)) return fail(JZ_EINVAL, "direction %d: %d nodes is too many", a, n[a]);
     if (!(d->hi[a] > d->lo[a])) return fail(JZ_EINVAL, "direction %d: empty extent", a);
   }
+  for (int f = 1; f < 6; ++f)
+    if (d->bc[f] == JZ_BC_INFLOW) return fail(JZ_EINVAL, "the inflow condition is supported on the x- face only");
   if (d->precision != JZ_P64 && d->precision != JZ_P32_M64 && d->precision != JZ_P32)
     return fail(JZ_EINVAL, "bad precision mode %d", d->precision);
   if (d->stretch_c != 0.0 && !(d->stretch_w > 0.0)) return fail(JZ_EINVAL, "stretch_w must be > 0");
@@ -104,6 +106,7 @@ static Carve carve(const jz_grid_desc* d) {
   c.off_sc = off; off = align256(off + sizeof(Scalars));
   c.off_partial = off; off = align256(off + sizeof(double) * RED_BLOCKS * DIAG_WORDS);
   c.off_tab = off; off = align256(off + sizeof(double) * c.tab_len);
+  c.off_inflow = off; off = align256(off + sizeof(double) * (size_t)L.n[1] * (size_t)L.n[2]);
   size_t qbytes = align256(5 * (size_t)L.npad * c.es);
   c.off_q0 = off; off += qbytes;
   c.off_qa = off; off += qbytes;
@@ -304,6 +307,7 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   d.M = g->base + cv.off_m;
   d.sc = (Scalars*)(g->base + cv.off_sc);
   d.partial = (double*)(g->base + cv.off_partial);
+  d.inflow = (double*)(g->base + cv.off_inflow);
   d.kc = default_kc(cv.L, d.prec);
   memset(&d.F, 0, sizeof(d.F));
   // coordinate tables

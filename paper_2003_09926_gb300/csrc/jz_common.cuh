@@ -77,7 +77,7 @@ struct Scalars {
   double diag[16];    // diagnostics result
 };
 
-constexpr int RED_BLOCKS = 304;   // fixed grid of the reductions (2 x 152 SMs)
+constexpr int RED_BLOCKS = 1216;  // fixed grid of the reductions (8 x 152 SMs)
 constexpr int RED_THREADS = 256;
 constexpr int DIAG_WORDS = 11;    // per-block diagnostics partial
 

@@ -215,8 +215,8 @@ __device__ void riemann_farfield(const FlowC& F, const T qi[5], const T n[3], T 
 // far field reads the nearest interior node and the face normal from the
 // metric terms at the boundary node.
 template <typename ST, typename MT>
-__device__ void boundary_value(const Layout& L, const Coords& C, const FlowC& F, const ST* __restrict__ Q,
-                               const MT* __restrict__ M, int i, int j, int k, ST qb[5]) {
+__device__ void boundary_value(const Layout& L, const double* __restrict__ inflow, const FlowC& F,
+                               const ST* __restrict__ Q, const MT* __restrict__ M, int i, int j, int k, ST qb[5]) {
   const int order[6] = {2, 3, 4, 5, 1, 0};
   int idx[3] = {i, j, k};
   int face = -1;
@@ -226,9 +226,8 @@ __device__ void boundary_value(const Layout& L, const Coords& C, const FlowC& F,
     int target = (f % 2 == 0) ? 0 : L.n[d] - 1;
     if (idx[d] == target) face = f;
   }
-  if (L.bc[face] == BC_INFLOW) {
-    double y = C.x(1, i, j, k), z = C.x(2, i, j, k);
-    double u = jet_profile(F, sqrt(y * y + z * z));
+  if (L.bc[face] == BC_INFLOW) {  // x- face only: profile tabulated per (j, k)
+    const double u = inflow[(long long)k * L.n[1] + j];
     to_conserved<ST>((ST)F.gm1, ST(1), (ST)u, ST(0), ST(0), (ST)(1.0 / F.gamma), qb);
     return;
   }
@@ -255,23 +254,79 @@ __device__ void boundary_value(const Layout& L, const Coords& C, const FlowC& F,
 // of the grid node its index maps to (wrap / clamp), and that node, when it
 // is a boundary node, takes its boundary-condition value.  Only interior
 // nodes are read, so the kernel is race-free in one launch.
+// Six boxes covering the padded nodes that lie inside an outer box [ol, oh]
+// but outside an inner box [il, ih] (z slabs over the whole outer plane, y
+// slabs over the inner k range, x slabs over the inner j, k range).
+struct Slabs {
+  int a[6][3], e[6][3];  // box origin and extent per slab
+};
+
+Slabs make_slabs(const int ol[3], const int oh[3], const int il[3], const int ih[3]) {
+  Slabs s;
+  const int E0 = oh[0] - ol[0] + 1, E1 = oh[1] - ol[1] + 1;
+  const int in1 = ih[1] - il[1] + 1, in2 = ih[2] - il[2] + 1;
+  auto box = [&](int q, int a0, int e0, int a1, int e1, int a2, int e2) {
+    s.a[q][0] = a0; s.e[q][0] = e0; s.a[q][1] = a1; s.e[q][1] = e1; s.a[q][2] = a2; s.e[q][2] = e2;
+  };
+  box(0, ol[0], E0, ol[1], E1, ol[2], il[2] - ol[2]);
+  box(1, ol[0], E0, ol[1], E1, ih[2] + 1, oh[2] - ih[2]);
+  box(2, ol[0], E0, ol[1], il[1] - ol[1], il[2], in2);
+  box(3, ol[0], E0, ih[1] + 1, oh[1] - ih[1], il[2], in2);
+  box(4, ol[0], il[0] - ol[0], il[1], in1, il[2], in2);
+  box(5, ih[0] + 1, oh[0] - ih[0], il[1], in1, il[2], in2);
+  return s;
+}
+
+__device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i, int& j, int& k) {
+  const int e0 = sl.e[q][0], e1 = sl.e[q][1];
+  if (t >= e0 * e1 * sl.e[q][2]) return false;
+  i = sl.a[q][0] + t % e0;
+  j = sl.a[q][1] + (t / e0) % e1;
+  k = sl.a[q][2] + t / (e0 * e1);
+  return true;
+}
+
+// Boundary fill, pass 1: every boundary node (a grid node outside the
+// updated box) takes its boundary-condition value.  Only interior nodes are
+// read, so the pass is race-free.
 template <typename ST, typename MT>
-__global__ void k_bc(Layout L, Shell s, Coords C, FlowC F, ST* __restrict__ Q, const MT* __restrict__ M) {
-  long long tot = s.total();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+__global__ void k_bc_nodes(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
+                           const MT* __restrict__ M) {
+  const int q = blockIdx.y;
+  const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int i, j, k;
-    shell_node(s, t, i, j, k);
-    int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]), mk = map_index(k, L.n[2], L.per[2]);
-    ST q[5];
-    bool inner = mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2];
-    if (inner) {
-      long long src = L.at(mi, mj, mk);
-      for (int v = 0; v < 5; ++v) q[v] = Q[(long long)v * L.npad + src];
-    } else {
-      boundary_value<ST, MT>(L, C, F, Q, M, mi, mj, mk, q);
-    }
-    long long g = L.at(i, j, k);
-    for (int v = 0; v < 5; ++v) Q[(long long)v * L.npad + g] = q[v];
+    slab_node(sl, q, t, i, j, k);
+    ST v[5];
+    boundary_value<ST, MT>(L, inflow, F, Q, M, i, j, k, v);
+    const long long g = L.at(i, j, k);
+    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = v[c];
+  }
+}
+
+// Boundary fill, pass 2: every ghost node copies the grid node its index
+// maps to (clamp, or wrap in periodic directions).
+template <typename ST>
+__global__ void k_ghosts(Layout L, Slabs sl, ST* __restrict__ Q) {
+  const int q = blockIdx.y;
+  const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    int i, j, k;
+    slab_node(sl, q, t, i, j, k);
+    const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
+    const int mk = map_index(k, L.n[2], L.per[2]);
+    const long long g = L.at(i, j, k), src = L.at(mi, mj, mk);
+    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = Q[(long long)c * L.npad + src];
+  }
+}
+
+// axial inflow velocity of the jet profile at the x- face nodes (FP64, once per state_init)
+__global__ void k_inflow(Layout L, Coords C, FlowC F, double* __restrict__ inflow) {
+  const int n = L.n[1] * L.n[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int j = t % L.n[1], k = t / L.n[1];
+    const double y = C.x(1, 0, j, k), z = C.x(2, 0, j, k);
+    inflow[t] = jet_profile(F, sqrt(y * y + z * z));
   }
 }
 
@@ -374,6 +429,8 @@ cudaError_t launch_metrics(const GridDev& g, cudaStream_t s) {
 
 cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
   long long N = (long long)g.L.n[0] * g.L.n[1] * g.L.n[2];
+  k_inflow<<<grid_blocks((long long)g.L.n[1] * g.L.n[2], 256), 256, 0, s>>>(g.L, g.C, g.F, g.inflow);
+  count_launches(1);
   if (g.prec == JZ_P64)
     k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0);
   else
@@ -383,14 +440,37 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
 }
 
 cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
-  Shell sh = make_shell(g.L, g.L.lo, g.L.hi);
-  int blocks = grid_blocks(sh.total(), 256);
+  const int pad_lo[3] = {-NG, -NG, -NG};
+  const int pad_hi[3] = {g.L.n[0] + 1, g.L.n[1] + 1, g.L.n[2] + 1};
+  const int grid_lo[3] = {0, 0, 0};
+  const int grid_hi[3] = {g.L.n[0] - 1, g.L.n[1] - 1, g.L.n[2] - 1};
+  const Slabs nodes = make_slabs(grid_lo, grid_hi, g.L.lo, g.L.hi);
+  const Slabs ghosts = make_slabs(pad_lo, pad_hi, grid_lo, grid_hi);
+  auto blocks_for = [](const Slabs& sl) {
+    long long big = 1;
+    for (int q = 0; q < 6; ++q) {
+      long long c = (long long)sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
+      big = c > big ? c : big;
+    }
+    int b = grid_blocks(big, 256);
+    return dim3(b < 1024 ? b : 1024, 6);
+  };
+  const dim3 bn = blocks_for(nodes), bg = blocks_for(ghosts);
   switch (g.prec) {
-    case JZ_P64: k_bc<double, double><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (double*)Q, (const double*)g.M); break;
-    case JZ_P32_M64: k_bc<float, double><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (float*)Q, (const double*)g.M); break;
-    default: k_bc<float, float><<<blocks, 256, 0, s>>>(g.L, sh, g.C, g.F, (float*)Q, (const float*)g.M); break;
+    case JZ_P64:
+      k_bc_nodes<double, double><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (double*)Q, (const double*)g.M);
+      k_ghosts<double><<<bg, 256, 0, s>>>(g.L, ghosts, (double*)Q);
+      break;
+    case JZ_P32_M64:
+      k_bc_nodes<float, double><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (float*)Q, (const double*)g.M);
+      k_ghosts<float><<<bg, 256, 0, s>>>(g.L, ghosts, (float*)Q);
+      break;
+    default:
+      k_bc_nodes<float, float><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (float*)Q, (const float*)g.M);
+      k_ghosts<float><<<bg, 256, 0, s>>>(g.L, ghosts, (float*)Q);
+      break;
   }
-  count_launches(1);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct GridDev {
   Coords C;            // coordinate tables
   Scalars* sc;         // device scalars
   double* partial;     // reduction partials: RED_BLOCKS * DIAG_WORDS doubles
+  double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)

@@ -48,13 +48,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, con
   const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
   const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
   const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
-  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   double best = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t % L.n[0]);
-    int j = (int)((t / L.n[0]) % L.n[1]);
-    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
-    long long n = L.at(i, j, k);
+  // warp w of the fixed grid visits rows r = w, w + W, ... (r = j + nj k); lanes walk i
+  const int lane = threadIdx.x & 31;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  const int rows = L.n[1] * L.n[2];
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += W) {
+    const long long row = L.at(0, r % L.n[1], r / L.n[1]);
+    for (int i = lane; i < L.n[0]; i += 32) {
+    const long long n = row + i;
     ST rho = Q[n], ri = ST(1) / rho;
     ST u = Q[L.npad + n] * ri, v = Q[2 * L.npad + n] * ri, w = Q[3 * L.npad + n] * ri;
     ST p = gm1 * (Q[4 * L.npad + n] - ST(0.5) * rho * (u * u + v * v + w * w));
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, con
     }
     double rate = (double)(conv + ST(2) * nu * Jn * Jn * s2);
     best = fmax(best, rate);
+    }
   }
   __shared__ double red[RED_THREADS / 32];
   best = warp_max(best);
@@ -81,10 +84,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, con
     for (int w = 1; w < RED_THREADS / 32; ++w) m = fmax(m, red[w]);
     partial[blockIdx.x] = m;
   }
-  if (last_block(&sc->count)) {
+  if (last_block(&sc->count)) {  // max is exact in any order
+    double m = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, ((volatile double*)partial)[b]);
+    m = warp_max(m);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double m = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) m = fmax(m, ((volatile double*)partial)[b]);
+      for (int w = 1; w < RED_THREADS / 32; ++w) m = fmax(m, red[w]);
+      m = fmax(m, red[0]);
       double dt = cfl / m;
       sc->dt = dt;
       sc->time += dt;
@@ -106,13 +115,15 @@ template <typename ST, typename MT>
 __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const ST* __restrict__ Q,
                                                       const MT* __restrict__ M, Scalars* sc, double* partial) {
   const double gm1 = F.gm1, g = F.gamma;
-  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   double acc[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t % L.n[0]);
-    int j = (int)((t / L.n[0]) % L.n[1]);
-    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
-    long long n = L.at(i, j, k);
+  // fixed visiting order: warp w takes rows w, w + W, ...; lanes walk i
+  const int lane = threadIdx.x & 31;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  const int rows = L.n[1] * L.n[2];
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += W) {
+    const long long row = L.at(0, r % L.n[1], r / L.n[1]);
+    for (int i = lane; i < L.n[0]; i += 32) {
+    const long long n = row + i;
     double q[5];
     bool finite = true;
     for (int v = 0; v < 5; ++v) {
@@ -129,6 +140,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
     acc[7] = fmin(acc[7], p);
     acc[8] = fmax(acc[8], p);
     acc[9] = fmax(acc[9], sqrt(u * u + v * v + w * w) / sqrt(g * p / rho));
+    }
   }
   __shared__ double sh[DIAG_WORDS][RED_THREADS];
   for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
@@ -149,20 +161,38 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
   if (threadIdx.x == 0)
     for (int c = 0; c < DIAG_WORDS; ++c) partial[(long long)blockIdx.x * DIAG_WORDS + c] = sh[c][0];
   if (last_block(&sc->dcount)) {
-    if (threadIdx.x == 0) {
-      volatile double* P = partial;
-      double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        const volatile double* x = P + (long long)b * DIAG_WORDS;
-        for (int c = 0; c < 5; ++c) r[c] += x[c];
-        r[5] = fmin(r[5], x[5]);
-        r[6] = fmax(r[6], x[6]);
-        r[7] = fmin(r[7], x[7]);
-        r[8] = fmax(r[8], x[8]);
-        r[9] = fmax(r[9], x[9]);
-        r[10] += x[10];
+    // thread t combines block records t, t + 256, ... in order, then the same
+    // fixed tree as above: a fixed summation order whichever block is last
+    const volatile double* P = partial;
+    double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const volatile double* x = P + (long long)b * DIAG_WORDS;
+      for (int c = 0; c < 5; ++c) r[c] += x[c];
+      r[5] = fmin(r[5], x[5]);
+      r[6] = fmax(r[6], x[6]);
+      r[7] = fmin(r[7], x[7]);
+      r[8] = fmax(r[8], x[8]);
+      r[9] = fmax(r[9], x[9]);
+      r[10] += x[10];
+    }
+    __syncthreads();
+    for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = r[c];
+    __syncthreads();
+    for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
+      if ((int)threadIdx.x < half) {
+        int o = threadIdx.x + half;
+        for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
+        sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
+        sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
+        sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
+        sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
+        sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
+        sh[10][threadIdx.x] += sh[10][o];
       }
-      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = r[c];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
       sc->dcount = 0;
     }
   }

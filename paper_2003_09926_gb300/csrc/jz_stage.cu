@@ -77,6 +77,41 @@ __device__ __forceinline__ KConst<R> make_kconst(const FlowC& F) {
 template <typename R>
 __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 
+// Elementary functions.  The FP32 kernel uses the hardware approximations
+// (sqrt.approx, rcp.approx, ex2/lg2.approx: a few ulp, far below the FP32
+// error of the scheme itself); the FP64 kernel keeps IEEE operations.
+template <typename R> struct Fn;
+template <> struct Fn<float> {
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
+  // J^(-2/3) = 2^(-2/3 log2 J), J > 0
+  static __device__ __forceinline__ float jm23(float J) {
+    float l, y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(J));
+    l *= -2.0f / 3.0f;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+    return y;
+  }
+};
+template <> struct Fn<double> {
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double jm23(double J) {
+    const double cb = cbrt(J);
+    return 1.0 / (cb * cb);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX, sm_90+ async proxy)
 // ---------------------------------------------------------------------------
@@ -214,14 +249,13 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
 #pragma unroll
       for (int m = 0; m < 3; ++m) g[q][m] = hJ * (S[m] * d0 + S[3 + m] * d1 + S[6 + m] * d2);
     }
-    const R mu = c.mu_inf * T * sqrt(T) * c.s1p1 / (T + c.s1);  // Sutherland
+    const R mu = Fn<R>::div(c.mu_inf * T * Fn<R>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     R mu_t = R(0);
     if (c.sgs) {  // Smagorinsky: rho (C_s Delta)^2 |S|, Delta = J^(-1/3), |S| = sqrt(2 S_ij S_ij)
       const R s12 = R(0.5) * (g[0][1] + g[1][0]), s13 = R(0.5) * (g[0][2] + g[2][0]);
       const R s23 = R(0.5) * (g[1][2] + g[2][1]);
       const R ss = g[0][0] * g[0][0] + g[1][1] * g[1][1] + g[2][2] * g[2][2] + R(2) * (s12 * s12 + s13 * s13 + s23 * s23);
-      const R cb = cbrt(Jn);
-      mu_t = rho * c.cs2 * sqrt(R(2) * ss) / (cb * cb);
+      mu_t = rho * c.cs2 * Fn<R>::sqrt_(R(2) * ss) * Fn<R>::jm23(Jn);
     }
     const R mue = mu + mu_t;
     const R kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
@@ -235,17 +269,17 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
   }
 
   R lam[3], U[3];
-  const R cson = sqrt(T);
+  const R cson = Fn<R>::sqrt_(T);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     U[k] = S[3 * k] * u + S[3 * k + 1] * v + S[3 * k + 2] * w;
-    const R sn = sqrt(S[3 * k] * S[3 * k] + S[3 * k + 1] * S[3 * k + 1] + S[3 * k + 2] * S[3 * k + 2]);
+    const R sn = Fn<R>::sqrt_(S[3 * k] * S[3 * k] + S[3 * k + 1] * S[3 * k + 1] + S[3 * k + 2] * S[3 * k + 2]);
     lam[k] = fabs(U[k]) + cson * sn;
   }
   R sq[3] = {R(0), R(0), R(0)};
   if (c.sig_half) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sq[k] = sqrt(lam[k]);
+    for (int k = 0; k < 3; ++k) sq[k] = Fn<R>::sqrt_(lam[k]);
   }
   const R m1 = rho * u, m2 = rho * v, m3 = rho * w;
 #pragma unroll
@@ -269,7 +303,7 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     if (k == 0) { pm = at(sC, V_P, 0, -1); pp = at(sC, V_P, 0, 1); }
     else if (k == 1) { pm = at(sC, V_P, -1, 0); pp = at(sC, V_P, 1, 0); }
     else { pm = at(sM, V_P, 0, 0); pp = at(sP, V_P, 0, 0); }
-    nu[k] = fabs(pp - R(2) * p + pm) / (pp + R(2) * p + pm);
+    nu[k] = Fn<R>::div(fabs(pp - R(2) * p + pm), pp + R(2) * p + pm);
   }
 }
 
@@ -378,7 +412,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
     R* dst = ring + ((p + 8) & 3) * NV * PL;
     for (int e = tid; e < PL; e += C::NT) {
       const R q0 = rq[e], q1 = rq[PL + e], q2 = rq[2 * PL + e], q3 = rq[3 * PL + e], q4 = rq[4 * PL + e];
-      const R ri = R(1) / q0;
+      const R ri = Fn<R>::rcp(q0);
       const R u = q1 * ri, v = q2 * ri, w = q3 * ri;
       const R pr = c.gm1 * (q4 - R(0.5) * q0 * (u * u + v * v + w * w));
       dst[V_RHO * PL + e] = q0;
@@ -390,11 +424,20 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
       dst[V_T * PL + e] = c.gamma * pr * ri;
     }
   };
-  auto fetch_plane = [&](int p) {  // wait for staged plane p, convert it, stage plane p + 2
+  // wait for staged plane p (and, when met_plane >= 0, the metrics of that
+  // plane) with one barrier, convert plane p, then stage plane p + 2
+  auto fetch_plane = [&](int p, int met_plane) {
     const int b = (p - pbase) & 1;
-    if (!wait_bar(b, ((p - pbase) >> 1) & 1)) return false;
+    bool ok = mbar_wait_bounded(&bar[b], ((p - pbase) >> 1) & 1);
+    if (ok && tid == 0) ++waited[b];
+    if (met_plane >= 0) {
+      const bool okm = ok && mbar_wait_bounded(&bar[2], (met_plane - (t0 - 1)) & 1);
+      if (okm && tid == 0) ++waited[2];
+      ok = okm;
+    }
+    if (__syncthreads_or(!ok)) return false;
     convert(p);
-    __syncthreads();  // raw buffer b consumed
+    __syncthreads();  // raw buffer b consumed, ring slot of p written
     if (p + 2 <= t1 + 1) issue_raw(p + 2);
     return true;
   };
@@ -506,9 +549,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
   R G3m[5], lt3m = 0, nu3m = 0, Jm = 0;
   R G3c[5], lt3c = 0, nu3c = 0, Jc = 0;
   R Rc[5], hprev[5];
-  if (!fetch_plane(t0 - 2) || !fetch_plane(t0 - 1) || !fetch_plane(t0) || !fetch_plane(t0 + 1)) {
-    failed = true;
-  } else if (!wait_bar(2, 0)) {
+  if (!fetch_plane(t0 - 2, -1) || !fetch_plane(t0 - 1, -1) || !fetch_plane(t0, -1) || !fetch_plane(t0 + 1, t0 - 1)) {
     failed = true;
   } else {
     node_pass(t0 - 1, G3m, lt3m, nu3m, Jm);
@@ -534,9 +575,9 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
 #pragma unroll
       for (int v = 0; v < 5; ++v) q0[v] = A.Q0[v * npad + n];
     }
-    __syncthreads();  // ring slot of plane t-2 and the face buffers are free
-    if (!fetch_plane(t + 2)) { failed = true; break; }
-    if (!wait_bar(2, (t + 1 - (t0 - 1)) & 1)) { failed = true; break; }
+    // the barrier inside fetch_plane also orders the previous iteration's
+    // reads of ring slot t-2 and of the face buffers before they are rewritten
+    if (!fetch_plane(t + 2, t + 1)) { failed = true; break; }
     R G3n[5], lt3n = 0, nu3n = 0, Jn = 0;
     node_pass(t + 1, G3n, lt3n, nu3n, Jn);
     __syncthreads();

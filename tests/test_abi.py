@@ -30,7 +30,7 @@ def test_grid_bytes_layout(L):
         pitch = (48 + 4 + 31) // 32 * 32
         npad = pitch * 36 * 36
         assert nb >= 3 * 5 * npad * es + 10 * npad * ms
-        assert nb <= 3 * 5 * npad * es + 10 * npad * ms + 64 * 1024 + 3 * 5 * 256 + 256
+        assert nb <= 3 * 5 * npad * es + 10 * npad * ms + 256 * 1024 + 32 * 32 * 8
 
 
 def test_paper_scale_footprint(L):

@@ -232,4 +232,4 @@ def test_launch_counter_advances(jz):
     before = jz.jz_launch_count()
     g.nsteps(3, cfl=0.5)
     g.synchronize()
-    assert jz.jz_launch_count() - before == 3 * 11
+    assert jz.jz_launch_count() - before == 3 * 16  # time step, 5 x (stage + boundary nodes + ghosts)
