@@ -159,11 +159,16 @@ int jz_state_download(jz_grid* g, double* host, size_t n);
  * parameters.  Synchronises the stream (host buffer may be reused on return). */
 int jz_state_upload(jz_grid* g, const double* host, size_t n);
 
-/* Batched execution of many grids in one launch per stage.  The batch
- * borrows the grids (which must share one precision mode and have flow
- * parameters set) and a caller-owned device buffer of jz_batch_bytes bytes
- * for its tile table; work goes to `stream`.  Every grid keeps its own CFL
- * time step, kept on the device. */
+/* Batched execution of many grids: per stage, one persistent launch whose
+ * CTAs take (grid, tile, k-chunk) work items from a device queue, largest
+ * first, plus one batched boundary fill; per step one batched time-step
+ * reduction.  The batch borrows the grids (one precision mode, flow
+ * parameters set; they must outlive the batch and keep the k-chunk length
+ * they had at jz_batch_create) and a caller-owned, 256-byte aligned device
+ * buffer of jz_batch_bytes bytes for its tables; work goes to `stream`
+ * (the grids' own streams are not used, so order them against it).  Every
+ * grid keeps its own CFL time step on the device, and its state is bitwise
+ * the one it reaches when stepped alone. */
 int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes);
 int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out);
 /* Enqueue n steps of every grid in the batch (graph-captured; asynchronous). */

@@ -13,6 +13,7 @@
 //   boundary fill of Q0
 // Stage 1 needs no boundary fill: Q^n already carries its boundary values,
 // which depend only on interior nodes.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -144,6 +145,10 @@ struct jz_grid {
 struct jz_batch {
   std::vector<jz_grid*> grids;
   cudaStream_t stream = nullptr;
+  int prec = 0;
+  char* dev = nullptr;
+  size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0;
+  int nitems = 0, bc_nodes_blocks = 1, bc_ghost_blocks = 1;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   double graph_cfl = -1.0;
@@ -187,10 +192,11 @@ int enqueue_step(jz_grid* g, double cfl, double dt_fixed) {
   cudaStream_t s = g->stream;
   int rc;
   if ((rc = timed(g, 2, [&] { return launch_timestep(d, cfl, dt_fixed, s); }))) return rc;
-  const int src[5] = {0, 1, 2, 1, 2};  // Q0, QA, QB, QA, QB
+  const int src[5] = {0, 1, 2, 1, 2};  // Q^(l-1): Q0, QA, QB, QA, QB
+  const int out[5] = {1, 2, 1, 2, 0};  // Q^(l):   QA, QB, QA, QB, Q0
   void* dst[5] = {d.QA, d.QB, d.QA, d.QB, d.Q0};
   for (int l = 0; l < 5; ++l) {
-    if ((rc = timed(g, 0, [&] { return launch_stage(d, l, src[l], dst[l], s); }))) return rc;
+    if ((rc = timed(g, 0, [&] { return launch_stage(d, l, src[l], out[l], s); }))) return rc;
     if ((rc = timed(g, 1, [&] { return launch_bc(d, dst[l], s); }))) return rc;
   }
   return JZ_OK;
@@ -460,7 +466,11 @@ int jz_diagnostics(jz_grid* g, jz_diag* out) {
   out->p_max = h.diag[8];
   out->mach_max = h.diag[9];
   out->nonfinite = (int64_t)h.diag[10];
-  if (h.err) return fail(JZ_ETIMEOUT, "a bounded device wait gave up (stage kernel data staging); results are invalid");
+  if (h.err)
+    return fail(JZ_ETIMEOUT,
+                "a bounded device wait gave up (stage kernel data staging: barrier %d parity %d plane %d tile %d,%d "
+                "chunk %d input %d); results are invalid",
+                h.errinfo[0], h.errinfo[1], h.errinfo[2], h.errinfo[3], h.errinfo[4], h.errinfo[5], h.errinfo[6]);
   if (out->nonfinite > 0) return fail(JZ_ENONFINITE, "%lld grid nodes hold non-finite values", (long long)out->nonfinite);
   return JZ_OK;
 }
@@ -547,43 +557,161 @@ int jz_set_tiling(jz_grid* g, int kc) {
   return JZ_OK;
 }
 
-// ---- batches: every grid's step sequence captured into one graph ----------
+// ---- batches: many grids per launch ----------------------------------------
 
-int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes) {
-  if (!grids || n < 1 || !bytes) return fail(JZ_EINVAL, "bad batch arguments");
-  *bytes = 256;
-  return JZ_OK;
-}
+}  // extern "C"
 
-int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out) {
-  if (!grids || n < 1 || !out) return fail(JZ_EINVAL, "bad batch arguments");
-  (void)dev_buf;
-  (void)bytes;
+namespace {
+
+struct BatchPlan {
+  size_t off_stage, off_bc, off_rate, off_items, off_queue, total;
+  std::vector<int4> items;
+};
+
+// Work items (grid, tile x, tile y, k-chunk) of every grid, largest first,
+// and the layout of the batch's device tables.
+int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
+  if (!grids || n < 1) return fail(JZ_EINVAL, "bad batch arguments");
   int prec = -1;
   for (int k = 0; k < n; ++k) {
     if (int rc = check_grid(grids[k], true)) return rc;
     if (prec >= 0 && grids[k]->dev.prec != prec) return fail(JZ_EINVAL, "batch grids must share one precision mode");
     prec = grids[k]->dev.prec;
   }
+  StageTiling t = stage_tiling(prec);
+  std::vector<std::pair<long long, int4>> work;
+  for (int k = 0; k < n; ++k) {
+    const Layout& L = grids[k]->dev.L;
+    const int kc = grids[k]->dev.kc;
+    const int tx = (L.hi[0] + t.ti) / t.ti, ty = (L.hi[1] + t.tj) / t.tj;
+    const int nz = L.hi[2] - L.lo[2] + 1, cz = (nz + kc - 1) / kc;
+    for (int bz = 0; bz < cz; ++bz) {
+      const int planes = (bz + 1) * kc <= nz ? kc : nz - bz * kc;
+      for (int by = 0; by < ty; ++by)
+        for (int bx = 0; bx < tx; ++bx) {
+          const int ox = std::min(L.hi[0], (bx + 1) * t.ti - 1) - std::max(L.lo[0], bx * t.ti) + 1;
+          const int oy = std::min(L.hi[1], (by + 1) * t.tj - 1) - std::max(L.lo[1], by * t.tj) + 1;
+          const long long cost = (long long)(planes + 3) * (ox > 0 ? ox : 0) * (oy > 0 ? oy : 0) + 1;
+          work.push_back({cost, make_int4(k, bx, by, bz)});
+        }
+    }
+  }
+  std::stable_sort(work.begin(), work.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  P.items.clear();
+  for (auto& w : work) P.items.push_back(w.second);
+  size_t off = 0;
+  P.off_stage = off; off = align256(off + (size_t)n * stage_ctx_bytes(prec));
+  P.off_bc = off; off = align256(off + (size_t)n * bc_ctx_bytes());
+  P.off_rate = off; off = align256(off + (size_t)n * rate_ctx_bytes());
+  P.off_items = off; off = align256(off + P.items.size() * sizeof(int4));
+  P.off_queue = off; off = align256(off + sizeof(unsigned int));
+  P.total = off;
+  return JZ_OK;
+}
+
+int enqueue_batch_step(jz_batch* b, double cfl) {
+  const int n = (int)b->grids.size();
+  cudaStream_t s = b->stream;
+  cudaError_t e = launch_timestep_batch(b->prec, b->dev + b->off_rate, n, cfl, s);
+  if (e != cudaSuccess) return fail(JZ_ECUDA, "batched time step launch failed: %s", cudaGetErrorString(e));
+  const int src[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
+  for (int l = 0; l < 5; ++l) {
+    e = launch_stage_batch(b->prec, b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
+                           (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
+    if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
+    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_nodes_blocks, b->bc_ghost_blocks, out[l], s);
+    if (e != cudaSuccess) return fail(JZ_ECUDA, "batched boundary launch failed: %s", cudaGetErrorString(e));
+  }
+  return JZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes) {
+  if (!bytes) return fail(JZ_EINVAL, "null output");
+  BatchPlan P;
+  if (int rc = batch_plan(grids, n, P)) return rc;
+  *bytes = P.total;
+  return JZ_OK;
+}
+
+int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out) {
+  if (!out) return fail(JZ_EINVAL, "null output");
+  *out = nullptr;
+  BatchPlan P;
+  if (int rc = batch_plan(grids, n, P)) return rc;
+  if (!dev_buf || ((uintptr_t)dev_buf & 255)) return fail(JZ_EINVAL, "batch buffer must be non-null and 256-byte aligned");
+  if (bytes < P.total) return fail(JZ_ENOMEM, "batch buffer holds %zu bytes, batch needs %zu", bytes, P.total);
+  const int prec = grids[0]->dev.prec;
+  std::vector<char> host(P.total, 0);
+  int nb = 1, gb = 1;
+  for (int k = 0; k < n; ++k) {
+    stage_ctx_fill(host.data() + P.off_stage + (size_t)k * stage_ctx_bytes(prec), grids[k]->dev);
+    int a = 1, c = 1;
+    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a, &c);
+    nb = std::max(nb, a);
+    gb = std::max(gb, c);
+    rate_ctx_fill(host.data() + P.off_rate + (size_t)k * rate_ctx_bytes(), grids[k]->dev);
+  }
+  memcpy(host.data() + P.off_items, P.items.data(), P.items.size() * sizeof(int4));
+  JZ_CUDA(cudaMemcpy(dev_buf, host.data(), P.total, cudaMemcpyHostToDevice));
   jz_batch* b = new (std::nothrow) jz_batch();
   if (!b) return fail(JZ_ENOMEM, "host allocation failed");
   b->grids.assign(grids, grids + n);
   b->stream = (cudaStream_t)stream;
+  b->prec = prec;
+  b->dev = (char*)dev_buf;
+  b->off_stage = P.off_stage;
+  b->off_bc = P.off_bc;
+  b->off_rate = P.off_rate;
+  b->off_items = P.off_items;
+  b->off_queue = P.off_queue;
+  b->nitems = (int)P.items.size();
+  b->bc_nodes_blocks = nb;
+  b->bc_ghost_blocks = gb;
   *out = b;
   return JZ_OK;
 }
 
 int jz_batch_nsteps(jz_batch* b, int n, double cfl) {
   if (!b) return fail(JZ_EINVAL, "null batch");
-  if (!(cfl > 0.0)) return fail(JZ_EINVAL, "batch steps need cfl > 0");
-  for (int s = 0; s < n; ++s)
-    for (jz_grid* g : b->grids) {
-      cudaStream_t keep = g->stream;
-      g->stream = b->stream;
-      int rc = enqueue_step(g, cfl, 0.0);
-      g->stream = keep;
-      if (rc) return rc;
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(JZ_EINVAL, "batch steps need a positive CFL number");
+  if (n < 0) return fail(JZ_EINVAL, "negative step count");
+  if (n == 0) return JZ_OK;
+  if (b->stream == nullptr) {  // the legacy stream cannot be captured
+    for (int s = 0; s < n; ++s)
+      if (int rc = enqueue_batch_step(b, cfl)) return rc;
+    return JZ_OK;
+  }
+  if (!b->exec || b->graph_cfl != cfl) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    uint64_t before = g_launches.load();
+    JZ_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_batch_step(b, cfl);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    g_launches.store(before);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return fail(JZ_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    b->graph = graph;
+    JZ_CUDA(cudaGraphInstantiate(&b->exec, graph, 0));
+    size_t nodes = 0;
+    JZ_CUDA(cudaGraphGetNodes(graph, nullptr, &nodes));
+    std::vector<cudaGraphNode_t> list(nodes);
+    JZ_CUDA(cudaGraphGetNodes(graph, list.data(), &nodes));
+    uint64_t kernels = 0;
+    for (auto nd : list) {
+      cudaGraphNodeType ty;
+      if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
     }
+    b->graph_kernels = kernels;
+    b->graph_cfl = cfl;
+  }
+  for (int s = 0; s < n; ++s) JZ_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  count_launches((uint64_t)n * b->graph_kernels);
   return JZ_OK;
 }
 

@@ -73,7 +73,7 @@ struct Scalars {
   unsigned int count; // last-block counter of the time-step reduction
   unsigned int dcount;// last-block counter of the diagnostics reduction
   int err;            // sticky device error flag
-  int pad;
+  int errinfo[7];     // first failure: barrier, parity, plane, tile x, tile y, chunk, stage input
   double diag[16];    // diagnostics result
 };
 

@@ -290,9 +290,8 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
 // updated box) takes its boundary-condition value.  Only interior nodes are
 // read, so the pass is race-free.
 template <typename ST, typename MT>
-__global__ void k_bc_nodes(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
-                           const MT* __restrict__ M) {
-  const int q = blockIdx.y;
+__device__ __forceinline__ void bc_nodes_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
+                                              const FlowC& F, ST* __restrict__ Q, const MT* __restrict__ M) {
   const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int i, j, k;
@@ -307,8 +306,7 @@ __global__ void k_bc_nodes(Layout L, Slabs sl, const double* __restrict__ inflow
 // Boundary fill, pass 2: every ghost node copies the grid node its index
 // maps to (clamp, or wrap in periodic directions).
 template <typename ST>
-__global__ void k_ghosts(Layout L, Slabs sl, ST* __restrict__ Q) {
-  const int q = blockIdx.y;
+__device__ __forceinline__ void ghosts_slab(const Layout& L, const Slabs& sl, int q, ST* __restrict__ Q) {
   const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int i, j, k;
@@ -318,6 +316,39 @@ __global__ void k_ghosts(Layout L, Slabs sl, ST* __restrict__ Q) {
     const long long g = L.at(i, j, k), src = L.at(mi, mj, mk);
     for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = Q[(long long)c * L.npad + src];
   }
+}
+
+template <typename ST, typename MT>
+__global__ void k_bc_nodes(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
+                           const MT* __restrict__ M) {
+  bc_nodes_slab<ST, MT>(L, sl, blockIdx.y, inflow, F, Q, M);
+}
+
+template <typename ST>
+__global__ void k_ghosts(Layout L, Slabs sl, ST* __restrict__ Q) {
+  ghosts_slab<ST>(L, sl, blockIdx.y, Q);
+}
+
+// batched versions: grid blockIdx.z of the table, state copy `which`
+struct BcCtx {
+  Layout L;
+  Slabs nodes, ghosts;
+  const double* inflow;
+  FlowC F;
+  void* Q[3];
+  const void* M;
+};
+
+template <typename ST, typename MT>
+__global__ void k_bc_nodes_batch(const BcCtx* __restrict__ ctx, int which) {
+  const BcCtx& X = ctx[blockIdx.z];
+  bc_nodes_slab<ST, MT>(X.L, X.nodes, blockIdx.y, X.inflow, X.F, (ST*)X.Q[which], (const MT*)X.M);
+}
+
+template <typename ST>
+__global__ void k_ghosts_batch(const BcCtx* __restrict__ ctx, int which) {
+  const BcCtx& X = ctx[blockIdx.z];
+  ghosts_slab<ST>(X.L, X.ghosts, blockIdx.y, (ST*)X.Q[which]);
 }
 
 // axial inflow velocity of the jet profile at the x- face nodes (FP64, once per state_init)
@@ -439,23 +470,29 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
+void bc_slabs(const Layout& L, Slabs& nodes, Slabs& ghosts) {
   const int pad_lo[3] = {-NG, -NG, -NG};
-  const int pad_hi[3] = {g.L.n[0] + 1, g.L.n[1] + 1, g.L.n[2] + 1};
+  const int pad_hi[3] = {L.n[0] + 1, L.n[1] + 1, L.n[2] + 1};
   const int grid_lo[3] = {0, 0, 0};
-  const int grid_hi[3] = {g.L.n[0] - 1, g.L.n[1] - 1, g.L.n[2] - 1};
-  const Slabs nodes = make_slabs(grid_lo, grid_hi, g.L.lo, g.L.hi);
-  const Slabs ghosts = make_slabs(pad_lo, pad_hi, grid_lo, grid_hi);
-  auto blocks_for = [](const Slabs& sl) {
-    long long big = 1;
-    for (int q = 0; q < 6; ++q) {
-      long long c = (long long)sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
-      big = c > big ? c : big;
-    }
-    int b = grid_blocks(big, 256);
-    return dim3(b < 1024 ? b : 1024, 6);
-  };
-  const dim3 bn = blocks_for(nodes), bg = blocks_for(ghosts);
+  const int grid_hi[3] = {L.n[0] - 1, L.n[1] - 1, L.n[2] - 1};
+  nodes = make_slabs(grid_lo, grid_hi, L.lo, L.hi);
+  ghosts = make_slabs(pad_lo, pad_hi, grid_lo, grid_hi);
+}
+
+int slab_blocks(const Slabs& sl) {
+  long long big = 1;
+  for (int q = 0; q < 6; ++q) {
+    long long c = (long long)sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
+    big = c > big ? c : big;
+  }
+  int b = grid_blocks(big, 256);
+  return b < 1024 ? b : 1024;
+}
+
+cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
+  Slabs nodes, ghosts;
+  bc_slabs(g.L, nodes, ghosts);
+  const dim3 bn(slab_blocks(nodes), 6), bg(slab_blocks(ghosts), 6);
   switch (g.prec) {
     case JZ_P64:
       k_bc_nodes<double, double><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (double*)Q, (const double*)g.M);
@@ -468,6 +505,45 @@ cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
     default:
       k_bc_nodes<float, float><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (float*)Q, (const float*)g.M);
       k_ghosts<float><<<bg, 256, 0, s>>>(g.L, ghosts, (float*)Q);
+      break;
+  }
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+size_t bc_ctx_bytes() { return sizeof(BcCtx); }
+
+// fills the host-side table entry; returns the block counts both passes need
+void bc_ctx_fill(void* dst, const GridDev& g, int* nodes_blocks, int* ghost_blocks) {
+  BcCtx& X = *(BcCtx*)dst;
+  X.L = g.L;
+  bc_slabs(g.L, X.nodes, X.ghosts);
+  X.inflow = g.inflow;
+  X.F = g.F;
+  X.Q[0] = g.Q0;
+  X.Q[1] = g.QA;
+  X.Q[2] = g.QB;
+  X.M = g.M;
+  *nodes_blocks = slab_blocks(X.nodes);
+  *ghost_blocks = slab_blocks(X.ghosts);
+}
+
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int nodes_blocks, int ghost_blocks, int which,
+                            cudaStream_t s) {
+  const dim3 bn(nodes_blocks, 6, n), bg(ghost_blocks, 6, n);
+  const BcCtx* X = (const BcCtx*)ctx;
+  switch (prec) {
+    case JZ_P64:
+      k_bc_nodes_batch<double, double><<<bn, 256, 0, s>>>(X, which);
+      k_ghosts_batch<double><<<bg, 256, 0, s>>>(X, which);
+      break;
+    case JZ_P32_M64:
+      k_bc_nodes_batch<float, double><<<bn, 256, 0, s>>>(X, which);
+      k_ghosts_batch<float><<<bg, 256, 0, s>>>(X, which);
+      break;
+    default:
+      k_bc_nodes_batch<float, float><<<bn, 256, 0, s>>>(X, which);
+      k_ghosts_batch<float><<<bg, 256, 0, s>>>(X, which);
       break;
   }
   count_launches(2);

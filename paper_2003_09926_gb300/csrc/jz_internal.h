@@ -55,15 +55,29 @@ cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s);
 cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s);
 cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
 
+// batched boundary fill over a device table of per-grid contexts
+size_t bc_ctx_bytes();
+void bc_ctx_fill(void* host_dst, const GridDev& g, int* nodes_blocks, int* ghost_blocks);
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int nodes_blocks, int ghost_blocks, int which,
+                            cudaStream_t s);
+
 // jz_reduce.cu
 cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s);
 cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s);
+size_t rate_ctx_bytes();
+void rate_ctx_fill(void* host_dst, const GridDev& g);
+cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, cudaStream_t s);
 
 // jz_stage.cu
 struct StageTiling { int ti, tj; };
 StageTiling stage_tiling(int prec);
-// qsel selects the input state Q^(l-1): 0 = Q0, 1 = QA, 2 = QB
-cudaError_t launch_stage(const GridDev& g, int stage, int qsel, void* Qout, cudaStream_t s);
+// qsel / qout select the input state Q^(l-1) and the output Q^(l): 0 = Q0, 1 = QA, 2 = QB
+cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s);
+// batched stage: a device table of per-grid stage contexts and work items
+size_t stage_ctx_bytes(int prec);
+void stage_ctx_fill(void* host_dst, const GridDev& g);
+cudaError_t launch_stage_batch(int prec, const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                               int stage, int qsel, int qout, cudaStream_t s);
 cudaError_t stage_configure();  // one-time kernel attributes (dynamic shared memory)
 
 }  // namespace jz

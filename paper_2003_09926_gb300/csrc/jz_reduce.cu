@@ -42,9 +42,8 @@ __device__ bool last_block(unsigned int* counter) {
 }
 
 template <typename ST, typename MT>
-__global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, const ST* __restrict__ Q,
-                                                          const MT* __restrict__ M, Scalars* sc, double* partial,
-                                                          double cfl) {
+__device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, const ST* __restrict__ Q,
+                                              const MT* __restrict__ M, Scalars* sc, double* partial, double cfl) {
   const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
   const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
   const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
@@ -101,6 +100,29 @@ __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, con
       sc->count = 0;
     }
   }
+}
+
+template <typename ST, typename MT>
+__global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, const ST* __restrict__ Q,
+                                                          const MT* __restrict__ M, Scalars* sc, double* partial,
+                                                          double cfl) {
+  timestep_body<ST, MT>(L, F, Q, M, sc, partial, cfl);
+}
+
+// batched: grid blockIdx.y of the table; gridDim.x blocks per grid
+struct RateCtx {
+  Layout L;
+  FlowC F;
+  const void* Q0;
+  const void* M;
+  Scalars* sc;
+  double* partial;
+};
+
+template <typename ST, typename MT>
+__global__ void __launch_bounds__(RED_THREADS) k_timestep_batch(const RateCtx* __restrict__ ctx, double cfl) {
+  const RateCtx& X = ctx[blockIdx.y];
+  timestep_body<ST, MT>(X.L, X.F, (const ST*)X.Q0, (const MT*)X.M, X.sc, X.partial, cfl);
 }
 
 __global__ void k_fixed_dt(Scalars* sc, double dt) {
@@ -219,6 +241,30 @@ cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaS
       k_timestep<float, float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
                                                                   g.sc, g.partial, cfl);
       break;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+size_t rate_ctx_bytes() { return sizeof(RateCtx); }
+
+void rate_ctx_fill(void* dst, const GridDev& g) {
+  RateCtx& X = *(RateCtx*)dst;
+  X.L = g.L;
+  X.F = g.F;
+  X.Q0 = g.Q0;
+  X.M = g.M;
+  X.sc = g.sc;
+  X.partial = g.partial;
+}
+
+cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, cudaStream_t s) {
+  const dim3 grid(64, n);  // 64 blocks per grid (partials hold RED_BLOCKS)
+  const RateCtx* X = (const RateCtx*)ctx;
+  switch (prec) {
+    case JZ_P64: k_timestep_batch<double, double><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
+    case JZ_P32_M64: k_timestep_batch<float, double><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
+    default: k_timestep_batch<float, float><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
   }
   count_launches(1);
   return cudaGetLastError();

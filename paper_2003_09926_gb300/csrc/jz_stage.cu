@@ -197,17 +197,31 @@ struct Cfg {
   static constexpr uint32_t MET_TX = sizeof(MT) * 10 * PL;
 };
 
+}  // namespace
+
+// Everything the stage kernel needs about one grid: TMA maps of the three
+// state copies and of the metrics, layout, state pointers, device scalars
+// (time step), flow constants and the k-chunk length.  Passed as a kernel
+// parameter for one grid, or read from a device table for a batch.
 template <typename R, typename MT>
-struct StageArgs {
+struct alignas(64) StageCtx {
+  CUtensorMap tmQ[3];  // Q0, QA, QB
+  CUtensorMap tmM;     // metrics
   Layout L;
-  const R* Q0;  // Q^(0) (may alias Qo in the last stage)
-  R* Qo;        // Q^(l)
+  R* Q[3];             // Q0, QA, QB
   const Scalars* sc;
-  int* err;     // sticky error flag (bounded-wait timeout)
-  double alpha;
-  int kc;
+  int* err;            // sticky error flag (bounded-wait timeout)
   FlowC F;
+  int kc;
 };
+
+// Per-launch stage selection: alpha_l, input copy Q^(l-1), output copy Q^(l).
+struct StageSel {
+  double alpha;
+  int qin, qout;
+};
+
+namespace {
 
 template <typename R, int RW, int PL>
 __device__ __forceinline__ R ring_at(const R* ring, int slot, int var, int y, int x) {
@@ -340,12 +354,15 @@ __device__ __forceinline__ void face5(const R* ring, const int so[4], const int 
   h[4] = face_h<R>(Ga[4], Gb[4], q[0], q[1], q[2], q[3], lam, e2, e4);
 }
 
+// One work item: the tile (bx, by) and k-chunk bz of grid X for stage st.
+// ph[] counts completed phases of the three mbarriers (identical in every
+// thread); issued[] / waited[] are kept by thread 0 for the timeout path.
 template <typename R, typename MT, int TI, int TJ>
-__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
-    k_stage(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmM, StageArgs<R, MT> A) {
+__device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const StageSel& st, int bx, int by, int bz,
+                                           unsigned char* smem, uint32_t ph[3], int issued[3], int waited[3],
+                                           bool& failed) {
   using C = Cfg<R, MT, TI, TJ>;
   constexpr int RW = C::RW, PL = C::PL, NTILE = C::NTILE;
-  extern __shared__ __align__(128) unsigned char smem[];
   R* raw[2] = {reinterpret_cast<R*>(smem + C::O_RAW0), reinterpret_cast<R*>(smem + C::O_RAW1)};
   MT* met = reinterpret_cast<MT*>(smem + C::O_MET);
   R* ring = reinterpret_cast<R*>(smem + C::O_RING);
@@ -357,12 +374,12 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
   R* Hj = reinterpret_cast<R*>(smem + C::O_HJ);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::O_BAR);  // [0],[1]: raw buffers, [2]: metrics
 
-  const Layout& L = A.L;
-  const KConst<R> c = make_kconst<R>(A.F);
+  const Layout& L = X.L;
+  const KConst<R> c = make_kconst<R>(X.F);
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;  // tile origin (node indices)
-  const int t0 = L.lo[2] + blockIdx.z * A.kc;
-  const int t1 = min(t0 + A.kc, L.hi[2] + 1);
+  const int i0 = bx * TI, j0 = by * TJ;  // tile origin (node indices)
+  const int t0 = L.lo[2] + bz * X.kc;
+  const int t1 = min(t0 + X.kc, L.hi[2] + 1);
   const int pbase = t0 - 2;  // first staged plane
 
   // node-pass role of this thread: tile node, j-halo node or i-halo node
@@ -373,23 +390,16 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
   const int gi = i0 + nx, gj = j0 + ny;
   const bool own = role == 0 && gi >= L.lo[0] && gi <= L.hi[0] && gj >= L.lo[1] && gj <= L.hi[1];
 
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_init(&bar[2], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  // staged plane p goes to raw buffer (p - pbase) & 1, completing phase ((p - pbase) >> 1) & 1
-  int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};  // per barrier, kept by thread 0 for the timeout path
+  // staged plane p goes to raw buffer (p - pbase) & 1; every barrier has at
+  // most one load in flight, so the parity to wait for is its count of
+  // completed phases ph[b] (kept identically by all threads) mod 2
   auto issue_raw = [&](int p) {
     if (tid == 0) {
       const int b = (p - pbase) & 1;
       ++issued[b];
       fence_async_shared();
       mbar_expect_tx(&bar[b], C::RAW_TX);
-      tma_load_4d(raw[b], &tmQ, &bar[b], i0, j0, p + NG, 0);
+      tma_load_4d(raw[b], &X.tmQ[st.qin], &bar[b], i0, j0, p + NG, 0);
     }
   };
   auto issue_met = [&](int p) {
@@ -397,12 +407,20 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
       ++issued[2];
       fence_async_shared();
       mbar_expect_tx(&bar[2], C::MET_TX);
-      tma_load_4d(met, &tmM, &bar[2], i0, j0, p + NG, 0);
+      tma_load_4d(met, &X.tmM, &bar[2], i0, j0, p + NG, 0);
     }
   };
-  bool failed = false;
-  auto wait_bar = [&](int b, uint32_t parity) {
-    const bool ok = mbar_wait_bounded(&bar[b], parity);
+  // on a bounded-wait timeout, the first failing CTA records where it gave up
+  auto record = [&](int b, int parity, int p) {
+    if (atomicCAS(X.err, 0, 1) == 0) {
+      int* info = X.err + 1;
+      info[0] = b; info[1] = parity; info[2] = p; info[3] = bx; info[4] = by; info[5] = bz; info[6] = st.qin;
+    }
+  };
+  auto wait_bar = [&](int b) {
+    const bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1);
+    if (!ok && tid == 0) record(b, ph[b] & 1, -100);
+    ++ph[b];
     if (ok && tid == 0) ++waited[b];
     return __syncthreads_or(!ok) == 0;
   };
@@ -424,14 +442,18 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
       dst[V_T * PL + e] = c.gamma * pr * ri;
     }
   };
-  // wait for staged plane p (and, when met_plane >= 0, the metrics of that
-  // plane) with one barrier, convert plane p, then stage plane p + 2
-  auto fetch_plane = [&](int p, int met_plane) {
+  // wait for staged plane p (and, when with_met, the metrics of plane
+  // met_plane) with one barrier, convert plane p, then stage plane p + 2
+  auto fetch_plane = [&](int p, bool with_met, int met_plane) {
     const int b = (p - pbase) & 1;
-    bool ok = mbar_wait_bounded(&bar[b], ((p - pbase) >> 1) & 1);
+    bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1);
+    if (!ok && tid == 0) record(b, ph[b] & 1, p);
+    ++ph[b];
     if (ok && tid == 0) ++waited[b];
-    if (met_plane >= 0) {
-      const bool okm = ok && mbar_wait_bounded(&bar[2], (met_plane - (t0 - 1)) & 1);
+    if (with_met) {
+      const bool okm = ok && mbar_wait_bounded(&bar[2], ph[2] & 1);
+      if (ok && !okm && tid == 0) record(2, ph[2] & 1, met_plane);
+      ++ph[2];
       if (okm && tid == 0) ++waited[2];
       ok = okm;
     }
@@ -539,8 +561,9 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
     face5<R, PL>(ring, so, oo, Ga, Gb, lam, e2, e4, h);
   };
 
-  const R adt = (R)(A.alpha * A.sc->dt);
+  const R adt = (R)(st.alpha * X.sc->dt);
   const long long npad = L.npad;
+  R* const Qo = X.Q[st.qout];
 
   // ---- prologue: stage planes t0-2 .. t0+1 and the metrics of t0-1
   issue_raw(t0 - 2);
@@ -549,13 +572,14 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
   R G3m[5], lt3m = 0, nu3m = 0, Jm = 0;
   R G3c[5], lt3c = 0, nu3c = 0, Jc = 0;
   R Rc[5], hprev[5];
-  if (!fetch_plane(t0 - 2, -1) || !fetch_plane(t0 - 1, -1) || !fetch_plane(t0, -1) || !fetch_plane(t0 + 1, t0 - 1)) {
+  if (!fetch_plane(t0 - 2, false, 0) || !fetch_plane(t0 - 1, false, 0) || !fetch_plane(t0, false, 0) ||
+      !fetch_plane(t0 + 1, true, t0 - 1)) {
     failed = true;
   } else {
     node_pass(t0 - 1, G3m, lt3m, nu3m, Jm);
     __syncthreads();  // metrics buffer and node buffers consumed
     issue_met(t0);
-    if (!wait_bar(2, 1)) {
+    if (!wait_bar(2)) {
       failed = true;
     } else {
       node_pass(t0, G3c, lt3c, nu3c, Jc);
@@ -573,11 +597,11 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
     if (own) {
       n = L.at(gi, gj, t);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) q0[v] = A.Q0[v * npad + n];
+      for (int v = 0; v < 5; ++v) q0[v] = X.Q[0][v * npad + n];
     }
     // the barrier inside fetch_plane also orders the previous iteration's
     // reads of ring slot t-2 and of the face buffers before they are rewritten
-    if (!fetch_plane(t + 2, t + 1)) { failed = true; break; }
+    if (!fetch_plane(t + 2, true, t + 1)) { failed = true; break; }
     R G3n[5], lt3n = 0, nu3n = 0, Jn = 0;
     node_pass(t + 1, G3n, lt3n, nu3n, Jn);
     __syncthreads();
@@ -589,7 +613,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
       kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, hk);
       if (own) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) A.Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
+        for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -603,16 +627,72 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
     }
   }
 
-  if (failed) {
-    // record the timeout and let copies still in flight land before exiting
-    if (tid == 0) {
-      atomicExch(A.err, 1);
-      for (int b = 0; b < 3; ++b)
-        for (int u = waited[b]; u < issued[b]; ++u)
-          if (!mbar_wait_bounded(&bar[b], u & 1)) break;
-    }
-    __syncthreads();
+}
+
+__device__ __forceinline__ void init_barriers(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+}
+
+// after a timeout: record it and let this CTA's copies still in flight land
+__device__ __forceinline__ void drain_after_timeout(uint64_t* bar, int* err, const int issued[3],
+                                                    const int waited[3]) {
+  if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+    for (int b = 0; b < 3; ++b)
+      for (int u = waited[b]; u < issued[b]; ++u)
+        if (!mbar_wait_bounded(&bar[b], u & 1)) break;  // phase u of barrier b
+  }
+  __syncthreads();
+}
+
+// One grid: one CTA per (tile, k-chunk).
+template <typename R, typename MT, int TI, int TJ>
+__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
+    k_stage(const __grid_constant__ StageCtx<R, MT> X, const StageSel st) {
+  using C = Cfg<R, MT, TI, TJ>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::O_BAR);
+  init_barriers(bar);
+  uint32_t ph[3] = {0, 0, 0};
+  int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};
+  bool failed = false;
+  stage_item<R, MT, TI, TJ>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
+  if (failed) drain_after_timeout(bar, X.err, issued, waited);
+}
+
+// Many grids: persistent CTAs (one per SM) take work items (grid, tile,
+// k-chunk) from a device queue, largest first.
+template <typename R, typename MT, int TI, int TJ>
+__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
+    k_stage_batch(const StageCtx<R, MT>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
+                  unsigned int* queue, const StageSel st) {
+  using C = Cfg<R, MT, TI, TJ>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::O_BAR);
+  __shared__ int next;
+  init_barriers(bar);
+  uint32_t ph[3] = {0, 0, 0};
+  int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};
+  bool failed = false;
+  int gsel = 0;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int it = next;
+    __syncthreads();
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    gsel = w.x;
+    stage_item<R, MT, TI, TJ>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
+    if (failed) break;
+  }
+  if (failed) drain_after_timeout(bar, ctx[gsel].err, issued, waited);
 }
 
 // tile shapes per precision (one CTA per SM)
@@ -621,26 +701,53 @@ constexpr int TI64 = 16, TJ64 = 16;  // FP64: 320 threads, 207 KB
 
 template <typename R, typename MT, int TI, int TJ>
 cudaError_t configure_one() {
-  return cudaFuncSetAttribute(k_stage<R, MT, TI, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg<R, MT, TI, TJ>::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<R, MT, TI, TJ>::BYTES);
 }
 
+const double kAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0};
+
+template <typename R, typename MT>
+void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
+  X.tmQ[0] = g.tmQ[0];
+  X.tmQ[1] = g.tmQ[1];
+  X.tmQ[2] = g.tmQ[2];
+  X.tmM = g.tmM;
+  X.L = g.L;
+  X.Q[0] = (R*)g.Q0;
+  X.Q[1] = (R*)g.QA;
+  X.Q[2] = (R*)g.QB;
+  X.sc = g.sc;
+  X.err = &g.sc->err;
+  X.F = g.F;
+  X.kc = g.kc;
+}
+
 template <typename R, typename MT, int TI, int TJ>
-cudaError_t launch_one(const GridDev& g, int stage, int qsel, void* Qout, cudaStream_t s) {
-  static const double alpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0};
+cudaError_t launch_one(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s) {
   using Cf = Cfg<R, MT, TI, TJ>;
-  StageArgs<R, MT> A;
-  A.L = g.L;
-  A.Q0 = (const R*)g.Q0;
-  A.Qo = (R*)Qout;
-  A.sc = g.sc;
-  A.err = &g.sc->err;
-  A.alpha = alpha[stage];
-  A.kc = g.kc;
-  A.F = g.F;
+  StageCtx<R, MT> X;
+  fill_ctx(X, g);
+  const StageSel st{kAlpha[stage], qsel, qout};
   const int nz = g.L.hi[2] - g.L.lo[2] + 1;
   dim3 grid((g.L.hi[0] + TI) / TI, (g.L.hi[1] + TJ) / TJ, (nz + g.kc - 1) / g.kc);
-  k_stage<R, MT, TI, TJ><<<grid, Cf::NT, Cf::BYTES, s>>>(g.tmQ[qsel], g.tmM, A);
+  k_stage<R, MT, TI, TJ><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R, typename MT, int TI, int TJ>
+cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue, int stage, int qsel,
+                         int qout, cudaStream_t s) {
+  using Cf = Cfg<R, MT, TI, TJ>;
+  const StageSel st{kAlpha[stage], qsel, qout};
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const int ctas = nitems < 152 ? nitems : 152;
+  k_stage_batch<R, MT, TI, TJ><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -660,11 +767,36 @@ cudaError_t stage_configure() {
   return cudaSuccess;
 }
 
-cudaError_t launch_stage(const GridDev& g, int stage, int qsel, void* Qout, cudaStream_t s) {
+cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s) {
   switch (g.prec) {
-    case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, Qout, s);
-    case JZ_P32_M64: return launch_one<float, double, TI32, TJ32>(g, stage, qsel, Qout, s);
-    default: return launch_one<float, float, TI32, TJ32>(g, stage, qsel, Qout, s);
+    case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, qout, s);
+    case JZ_P32_M64: return launch_one<float, double, TI32, TJ32>(g, stage, qsel, qout, s);
+    default: return launch_one<float, float, TI32, TJ32>(g, stage, qsel, qout, s);
+  }
+}
+
+size_t stage_ctx_bytes(int prec) {
+  switch (prec) {
+    case JZ_P64: return sizeof(StageCtx<double, double>);
+    case JZ_P32_M64: return sizeof(StageCtx<float, double>);
+    default: return sizeof(StageCtx<float, float>);
+  }
+}
+
+void stage_ctx_fill(void* dst, const GridDev& g) {
+  switch (g.prec) {
+    case JZ_P64: fill_ctx(*(StageCtx<double, double>*)dst, g); break;
+    case JZ_P32_M64: fill_ctx(*(StageCtx<float, double>*)dst, g); break;
+    default: fill_ctx(*(StageCtx<float, float>*)dst, g); break;
+  }
+}
+
+cudaError_t launch_stage_batch(int prec, const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                               int stage, int qsel, int qout, cudaStream_t s) {
+  switch (prec) {
+    case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
+    case JZ_P32_M64: return launch_batch<float, double, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
+    default: return launch_batch<float, float, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
   }
 }
 
