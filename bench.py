@@ -202,6 +202,81 @@ def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
                       f"grid in FP64, OpenMP over k-planes, {sec:.1f} s"}
 
 
+def bench_batched(jz, torch, W, local: int, steps: int, steps64: int, cfl: float = 0.5):
+    """64 uneven jet grids (32^3 .. 160x128x128), FP32, one persistent launch
+    per stage for all grids (graph-replayed), against plain FP64 one grid at a
+    time.  The k-chunk length is chosen by the autotuner."""
+    from paper_2003_09926_gb300 import autotune
+    cfg = W.config3()
+    cases = [(c["grid"], c["flow"]) for c in cfg["cases"]]
+    kc = autotune.tune_batch(cases, cfl=cfl, device=local)
+    stream = torch.cuda.Stream(device=local)
+    grids = [jz.Grid(c["grid"], stream=stream, device=local).init(c["flow"], c["seed"]) for c in cfg["cases"]]
+    for g in grids:
+        autotune.apply_kc(g, kc)
+    pts = sum(interior_points(c["grid"]) for c in cfg["cases"])
+    b = jz.Batch(grids, stream=stream)
+    b.nsteps(3, cfl)  # warm-up and graph capture
+    stream.synchronize()
+    l0 = jz.jz_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.nsteps(steps, cfl)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = jz.jz_launch_count() - l0
+    b.close()
+    for g in grids:
+        g.close()
+    # plain FP64, one grid at a time (graph-replayed single-grid steps)
+    s64 = torch.cuda.Stream(device=local)
+    g64 = [jz.Grid(dict(c["grid"], precision=W.P64), stream=s64, device=local).init(c["flow"], c["seed"])
+           for c in cfg["cases"]]
+    for g in g64:
+        g.nsteps(1, cfl=cfl)
+    s64.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(s64)
+    for g in g64:
+        g.nsteps(steps64, cfl=cfl)
+    f1.record(s64)
+    f1.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    for g in g64:
+        g.close()
+    v32 = pts * 5 * steps / (ms / 1e3) / 1e6
+    v64 = pts * 5 * steps64 / (ms64 / 1e3) / 1e6
+    return {"workload": "c3: 64 jet grids 32^3..160x128x128 (seed 3), M~U[1.2,2], Re~U[5e5,2e6]",
+            "points_updated": pts, "fp32_batched": {"value": v32, "unit": UNIT, "steps": steps, "ms": ms,
+                                                    "kernel_launches": launches, "kc": kc,
+                                                    "launches_per_step": launches / steps},
+            "fp64_one_grid_at_a_time": {"value": v64, "unit": UNIT, "steps": steps64, "ms": ms64},
+            "speedup": v32 / v64}
+
+
+def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6):
+    """Continuous batching on a bounded serving trace: log-uniform 1e5..2e6
+    points per case, 50..500 steps, Poisson arrivals at 70% of the measured
+    batched capacity, 150 GB HBM budget, 10-step slices; against the same
+    trace one case at a time (FP32 unbatched, and FP64 on its first cases)."""
+    from paper_2003_09926_gb300 import serve
+    cfg = W.config4(nreq=nreq, pts_hi=2e6)
+    work = np.mean([interior_points(r["grid"]) * 5 * r["steps"] for r in cfg["requests"]])
+    rate = 0.7 * capacity * 1e6 / work
+    trace = serve.poisson_trace(cfg, rate)
+    srv = serve.Server(150 * 10**9, slice_steps=10, device=local)
+    res = srv.run(trace)
+    out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..2e6 points, 50..500 steps, seed 4",
+           "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10,
+           "fp32_continuous_batching": serve.summarize(res), "peak_resident_bytes": srv.peak_bytes,
+           "slices": srv.slices}
+    out["fp32_one_at_a_time"] = serve.summarize(serve.serve_one_at_a_time(trace, W.P32, device=local))
+    out["fp64_one_at_a_time_first_cases"] = dict(
+        serve.summarize(serve.serve_one_at_a_time(trace[:base64_n], W.P64, device=local)), cases=base64_n)
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU FP64 oracle on the host cores, same metric."""
     if rank != 0:
@@ -243,6 +318,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (default steps/10)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-grid batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -370,6 +447,11 @@ def main(argv=None):
             "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
                                    "interior": "nodes at least 3 from every face; far-field face nodes can differ by O(1) where the Riemann condition switches branch (sign of u_n, |u_n| = c) between precisions"},
             "fp64_vs_fp32_speedup": results[head]["value"] / results[W.P64]["value"]}
+    if not args.no_batched:
+        line["batched"] = bench_batched(jz, torch, W, local, steps=max(10, args.steps // 5), steps64=2)
+    if not args.no_serving:
+        cap = line["batched"]["fp32_batched"]["value"] if "batched" in line else results[head]["value"]
+        line["serving"] = bench_serving(jz, torch, W, local, cap)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_baseline(cfg)
     if rank == 0:

@@ -275,6 +275,7 @@ class Grid:
         if getattr(self, "h", None):
             jz_grid_destroy(self.h)
             self.h = None
+        self.buf = None  # return the device memory to the caller's allocator
 
     def __del__(self):
         try:
@@ -305,3 +306,4 @@ class Batch:
         if getattr(self, "h", None):
             lib().jz_batch_destroy(self.h)
             self.h = None
+        self.buf = None

@@ -1,0 +1,190 @@
+"""Continuous-batching request loop for jet cases.
+
+Requests (a grid, flow parameters, a seed, a step count and an arrival time)
+are admitted in arrival order while their device footprint (``jz_grid_bytes``)
+fits an HBM budget; admitted cases stay resident on the device and advance
+together in time slices, each slice one batched launch sequence over every
+resident grid (``jz_batch_nsteps``).  Finished cases are retired at slice
+boundaries -- their diagnostics (and optionally their state) are read back
+and their memory returned -- so cases that arrive while others run are
+admitted as soon as memory frees up and their work overlaps on the device.
+A case's result does not depend on the mix it ran in: the per-point
+arithmetic of the batched kernels is that of a grid stepped alone.
+
+Latency of a case = completion - arrival (wall clock, seconds).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import jz
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    grid: dict
+    flow: dict
+    seed: int
+    steps: int
+    arrival: float = 0.0
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    status: str            # "done" or "rejected: <why>"
+    arrival: float
+    admitted: float = float("nan")
+    finished: float = float("nan")
+    points: int = 0
+    steps: int = 0
+    diag: dict | None = None
+    state: np.ndarray | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def updated_points(grid: dict) -> int:
+    n = 1
+    for a, key in enumerate(("ni", "nj", "nk")):
+        n *= grid[key] if grid["bc"][2 * a] == W.BC_PERIODIC else grid[key] - 2
+    return n
+
+
+class Server:
+    def __init__(self, budget_bytes: int, slice_steps: int = 10, cfl: float = 0.5, device: int = 0,
+                 keep_state: bool = False, kc_for=None):
+        import torch  # device memory and the stream only
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.slice_steps = int(slice_steps)
+        self.cfl = float(cfl)
+        self.device = device
+        self.keep_state = keep_state
+        self.kc_for = kc_for  # optional callable grid-desc -> k-chunk length (autotuner)
+        self.stream = torch.cuda.Stream(device=device)
+        self.peak_bytes = 0
+        self.slices = 0
+
+    def run(self, requests: list[Request]) -> list[Result]:
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        results: dict[int, Result] = {}
+        resident: list[dict] = []
+        used = 0
+        batch, batch_key = None, None
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending or resident:
+            # admit in arrival order while the budget allows
+            while pending and pending[0].arrival <= now():
+                r = pending[0]
+                need = jz.jz_grid_bytes(r.grid)
+                if need > self.budget:
+                    pending.pop(0)
+                    results[r.rid] = Result(r.rid, f"rejected: needs {need} bytes, budget {self.budget}", r.arrival)
+                    continue
+                if used + need > self.budget:
+                    break
+                pending.pop(0)
+                g = jz.Grid(r.grid, stream=self.stream, device=self.device).init(r.flow, r.seed)
+                if self.kc_for is not None:
+                    jz.jz_set_tiling(g.h, int(self.kc_for(r.grid)))
+                used += need
+                self.peak_bytes = max(self.peak_bytes, used)
+                resident.append(dict(req=r, grid=g, left=r.steps, bytes=need))
+                results[r.rid] = Result(r.rid, "running", r.arrival, admitted=now(), points=updated_points(r.grid),
+                                        steps=r.steps)
+            if not resident:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
+                continue
+            key = tuple(c["req"].rid for c in resident)
+            if key != batch_key:
+                if batch is not None:
+                    batch.close()
+                batch = jz.Batch([c["grid"] for c in resident], stream=self.stream)
+                batch_key = key
+            n = min(self.slice_steps, min(c["left"] for c in resident))
+            batch.nsteps(n, self.cfl)
+            self.stream.synchronize()
+            self.slices += 1
+            still = []
+            for c in resident:
+                c["left"] -= n
+                if c["left"] > 0:
+                    still.append(c)
+                    continue
+                res = results[c["req"].rid]
+                res.diag = c["grid"].diagnostics(allow_nonfinite=True)
+                if self.keep_state:
+                    res.state = c["grid"].download()
+                res.finished = now()
+                res.status = "done"
+                c["grid"].close()
+                used -= c["bytes"]
+            if len(still) != len(resident):
+                resident = still
+                if batch is not None:
+                    batch.close()
+                batch, batch_key = None, None
+        if batch is not None:
+            batch.close()
+        return [results[k] for k in sorted(results)]
+
+
+def serve_one_at_a_time(requests: list[Request], precision: int, cfl: float = 0.5, device: int = 0,
+                        keep_state: bool = False) -> list[Result]:
+    """The plain baseline: requests in arrival order, one grid at a time, each
+    run to completion with graph-replayed single-grid steps."""
+    import torch
+    stream = torch.cuda.Stream(device=device)
+    out = []
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0
+    for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        while now() < r.arrival:
+            time.sleep(min(0.01, r.arrival - now()))
+        start = now()
+        g = jz.Grid(dict(r.grid, precision=precision), stream=stream, device=device).init(r.flow, r.seed)
+        g.nsteps(r.steps, cfl=cfl)
+        stream.synchronize()
+        res = Result(r.rid, "done", r.arrival, admitted=start, points=updated_points(r.grid), steps=r.steps)
+        res.diag = g.diagnostics(allow_nonfinite=True)
+        if keep_state:
+            res.state = g.download()
+        res.finished = now()
+        g.close()
+        out.append(res)
+    return out
+
+
+def summarize(results: list[Result]) -> dict:
+    done = [r for r in results if r.status == "done"]
+    if not done:
+        return {"completed": 0}
+    lat = np.array([r.latency for r in done])
+    span = max(r.finished for r in done) - min(r.arrival for r in done)
+    work = sum(r.points * 5 * r.steps for r in done)
+    return {"completed": len(done), "rejected": len(results) - len(done),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "makespan_s": float(span),
+            "throughput_mpt_stage_s": work / span / 1e6 if span > 0 else None}
+
+
+def poisson_trace(cfg: dict, rate_hz: float, seed: int = 4) -> list[Request]:
+    """Attach seeded Poisson arrival times (mean rate rate_hz) to a serving
+    configuration's requests."""
+    rng = np.random.default_rng(seed + 1000)
+    t = 0.0
+    reqs = []
+    for i, r in enumerate(cfg["requests"]):
+        t += float(rng.exponential(1.0 / rate_hz))
+        reqs.append(Request(i, r["grid"], r["flow"], r["seed"], r["steps"], t))
+    return reqs

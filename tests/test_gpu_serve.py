@@ -1,0 +1,61 @@
+"""Continuous batching: cases arriving while others run are admitted as
+memory frees up (HBM budget), advance together in time slices, and each
+case's final state is bitwise the one it reaches when run alone."""
+import numpy as np
+import pytest
+
+from paper_2003_09926_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_09926_gb300 import build, jz, serve
+    build.build()
+    jz.lib()
+    return jz, serve
+
+
+def _trace(serve):
+    shapes = [(40, 24, 20), (33, 17, 19), (24, 24, 24), (20, 40, 12), (48, 16, 24), (30, 20, 16)]
+    steps = [12, 7, 23, 9, 15, 11]
+    arrivals = [0.0, 0.0, 0.02, 0.05, 0.05, 0.1]
+    reqs = []
+    for i, (sh, n, t) in enumerate(zip(shapes, steps, arrivals)):
+        flow = W.jet_flow(mach=1.2 + 0.1 * i, re=5e5 + 2e5 * i)
+        reqs.append(serve.Request(i, W.jet_grid(*sh, map_amp=0.02, map_seed=i, precision=W.P32), flow, 50 + i, n,
+                                  t))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix(mods):
+    jz, serve = mods
+    reqs = _trace(serve)
+    sizes = sorted(jz.jz_grid_bytes(r.grid) for r in reqs)
+    budget = sizes[-1] + sizes[-2] + sizes[-3]  # at most about three cases resident
+    srv = serve.Server(budget, slice_steps=5, keep_state=True)
+    res = srv.run(reqs)
+    assert all(r.status == "done" for r in res)
+    assert srv.peak_bytes <= budget and srv.slices > 3
+    for r, q in zip(res, reqs):
+        alone = jz.Grid(q.grid).init(q.flow, q.seed)
+        alone.nsteps(q.steps, cfl=0.5)
+        np.testing.assert_array_equal(r.state, alone.download())
+        assert r.diag["step"] == q.steps and r.latency > 0
+        alone.close()
+    s = serve.summarize(res)
+    assert s["completed"] == 6 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_over_budget_request_rejected(mods):
+    jz, serve = mods
+    reqs = _trace(serve)[:3]
+    need = jz.jz_grid_bytes(reqs[0].grid)
+    srv = serve.Server(need - 1, slice_steps=4)
+    res = srv.run(reqs)
+    assert res[0].status.startswith("rejected")
+    assert all(r.status == "done" for r in res[1:] if jz.jz_grid_bytes(reqs[r.rid].grid) < need)
