@@ -219,7 +219,7 @@ int default_kc(const Layout& L, int prec) {
   StageTiling t = stage_tiling(prec);
   long long tiles = (long long)((L.hi[0] + t.ti) / t.ti) * ((L.hi[1] + t.tj) / t.tj);
   int nz = L.hi[2] - L.lo[2] + 1;
-  long long slots = 152LL;  // one stage CTA per SM
+  long long slots = 152LL * stage_ctas_per_sm(prec);
   int best = nz;
   double best_cost = 1e300;
   for (int kc = 1; kc <= nz; ++kc) {

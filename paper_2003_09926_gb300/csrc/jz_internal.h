@@ -71,6 +71,7 @@ cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, 
 // jz_stage.cu
 struct StageTiling { int ti, tj; };
 StageTiling stage_tiling(int prec);
+int stage_ctas_per_sm(int prec);
 // qsel / qout select the input state Q^(l-1) and the output Q^(l): 0 = Q0, 1 = QA, 2 = QB
 cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s);
 // batched stage: a device table of per-grid stage contexts and work items

@@ -54,7 +54,7 @@ struct KConst {
 };
 
 template <typename R>
-__device__ __forceinline__ KConst<R> make_kconst(const FlowC& F) {
+__host__ __device__ inline KConst<R> make_kconst(const FlowC& F) {
   KConst<R> c;
   c.gamma = (R)F.gamma;
   c.gm1 = (R)F.gm1;
@@ -193,6 +193,8 @@ struct Cfg {
   static constexpr size_t O_HJ = O_HI + HI_B;
   static constexpr size_t O_BAR = O_HJ + HJ_B;
   static constexpr size_t BYTES = O_BAR + 128;
+  // CTAs per SM that fit (227 KB per SM, ~1 KB reserved per CTA)
+  static constexpr int MINB = 2 * (BYTES + 1024 + 128) <= 232448 ? 2 : 1;
   static constexpr uint32_t RAW_TX = sizeof(R) * 5 * PL;
   static constexpr uint32_t MET_TX = sizeof(MT) * 10 * PL;
 };
@@ -212,6 +214,7 @@ struct alignas(64) StageCtx {
   const Scalars* sc;
   int* err;            // sticky error flag (bounded-wait timeout)
   FlowC F;
+  KConst<R> k;         // flow constants in the arithmetic type, prepared on the host
   int kc;
 };
 
@@ -375,7 +378,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::O_BAR);  // [0],[1]: raw buffers, [2]: metrics
 
   const Layout& L = X.L;
-  const KConst<R> c = make_kconst<R>(X.F);
+  const KConst<R> c = X.k;
   const int tid = threadIdx.x;
   const int i0 = bx * TI, j0 = by * TJ;  // tile origin (node indices)
   const int t0 = L.lo[2] + bz * X.kc;
@@ -653,7 +656,7 @@ __device__ __forceinline__ void drain_after_timeout(uint64_t* bar, int* err, con
 
 // One grid: one CTA per (tile, k-chunk).
 template <typename R, typename MT, int TI, int TJ>
-__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
+__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage(const __grid_constant__ StageCtx<R, MT> X, const StageSel st) {
   using C = Cfg<R, MT, TI, TJ>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -669,7 +672,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
 // Many grids: persistent CTAs (one per SM) take work items (grid, tile,
 // k-chunk) from a device queue, largest first.
 template <typename R, typename MT, int TI, int TJ>
-__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
+__global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage_batch(const StageCtx<R, MT>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
                   unsigned int* queue, const StageSel st) {
   using C = Cfg<R, MT, TI, TJ>;
@@ -696,7 +699,10 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, 1)
 }
 
 // tile shapes per precision (one CTA per SM)
-constexpr int TI32 = 32, TJ32 = 16;  // FP32: 608 threads, 191 KB (FP32 metrics) / 220 KB (FP64 metrics)
+// (a 32 x 8 FP32 tile with two CTAs per SM measured slower: the larger halo
+// share outweighs the overlap of the two CTAs' barriers)
+constexpr int TI32 = 32, TJ32 = 16;  // P32: 608 threads, 191 KB: one CTA per SM
+constexpr int TIM = 32, TJM = 16;    // P32_M64: 608 threads, 220 KB (FP64 metric staging): one CTA per SM
 constexpr int TI64 = 16, TJ64 = 16;  // FP64: 320 threads, 207 KB
 
 template <typename R, typename MT, int TI, int TJ>
@@ -723,6 +729,7 @@ void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
   X.sc = g.sc;
   X.err = &g.sc->err;
   X.F = g.F;
+  X.k = make_kconst<R>(g.F);
   X.kc = g.kc;
 }
 
@@ -746,7 +753,7 @@ cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigne
   const StageSel st{kAlpha[stage], qsel, qout};
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  const int ctas = nitems < 152 ? nitems : 152;
+  const int ctas = nitems < 152 * Cf::MINB ? nitems : 152 * Cf::MINB;
   k_stage_batch<R, MT, TI, TJ><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
@@ -754,15 +761,24 @@ cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigne
 
 }  // namespace
 
+int stage_ctas_per_sm(int prec) {
+  switch (prec) {
+    case JZ_P64: return Cfg<double, double, TI64, TJ64>::MINB;
+    case JZ_P32_M64: return Cfg<float, double, TIM, TJM>::MINB;
+    default: return Cfg<float, float, TI32, TJ32>::MINB;
+  }
+}
+
 StageTiling stage_tiling(int prec) {
   if (prec == JZ_P64) return {TI64, TJ64};
+  if (prec == JZ_P32_M64) return {TIM, TJM};
   return {TI32, TJ32};
 }
 
 cudaError_t stage_configure() {
   cudaError_t e;
   if ((e = configure_one<double, double, TI64, TJ64>()) != cudaSuccess) return e;
-  if ((e = configure_one<float, double, TI32, TJ32>()) != cudaSuccess) return e;
+  if ((e = configure_one<float, double, TIM, TJM>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -770,7 +786,7 @@ cudaError_t stage_configure() {
 cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s) {
   switch (g.prec) {
     case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, qout, s);
-    case JZ_P32_M64: return launch_one<float, double, TI32, TJ32>(g, stage, qsel, qout, s);
+    case JZ_P32_M64: return launch_one<float, double, TIM, TJM>(g, stage, qsel, qout, s);
     default: return launch_one<float, float, TI32, TJ32>(g, stage, qsel, qout, s);
   }
 }
@@ -795,7 +811,7 @@ cudaError_t launch_stage_batch(int prec, const void* ctx, const int4* items, int
                                int stage, int qsel, int qout, cudaStream_t s) {
   switch (prec) {
     case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
-    case JZ_P32_M64: return launch_batch<float, double, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
+    case JZ_P32_M64: return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, s);
     default: return launch_batch<float, float, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
   }
 }
