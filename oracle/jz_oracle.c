@@ -154,6 +154,7 @@ void orc_coords(const orc_grid* g, double* X) {
   int m[9];
   double th[9];
   orc_map_params(g, m, th);
+#pragma omp parallel for schedule(static)
   for (int k = -NG; k < g->nk + NG; ++k)
     for (int j = -NG; j < g->nj + NG; ++j)
       for (int i = -NG; i < g->ni + NG; ++i) {
@@ -201,6 +202,7 @@ static void fill_ghosts(const orc_grid* g, double* F, int ncomp) {
  * Computed at every grid node 0..N-1, then ghost entries by the node map. */
 void orc_metrics(const orc_grid* g, const double* X, double* S /* 9 x npad */, double* J) {
   size_t np = orc_npad(g);
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < g->nk; ++k)
     for (int j = 0; j < g->nj; ++j)
       for (int i = 0; i < g->ni; ++i) {
@@ -320,6 +322,7 @@ static int winning_face(const orc_grid* g, const int idx[3]) {
 void orc_apply_bc(const orc_grid* g, const orc_flow* f, const double* X, const double* S, double* Q) {
   size_t np = orc_npad(g);
   /* boundary nodes: read only interior nodes, so the order of nodes is free */
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < g->nk; ++k)
     for (int j = 0; j < g->nj; ++j)
       for (int i = 0; i < g->ni; ++i) {
@@ -602,7 +605,8 @@ int orc_residual(const orc_grid* g, const orc_flow* f, const double* S, const do
 double orc_max_rate(const orc_grid* g, const orc_flow* f, const double* S, const double* J, const double* Q) {
   size_t np = orc_npad(g);
   double vfac = (4.0 / 3.0 > f->gamma / f->pr) ? 4.0 / 3.0 : f->gamma / f->pr;
-  double best = 0.0;
+  double best = 0.0; /* a maximum: the same in any order */
+#pragma omp parallel for schedule(static) reduction(max : best)
   for (int k = 0; k < g->nk; ++k)
     for (int j = 0; j < g->nj; ++j)
       for (int i = 0; i < g->ni; ++i) {
@@ -644,6 +648,7 @@ double orc_rk_step(const orc_grid* g, const orc_flow* f, const double* X, const 
     /* Q holds Q^(l-1); boundary nodes are set at the start of every stage */
     orc_apply_bc(g, f, X, S, Q);
     if (orc_residual(g, f, S, J, Q, R)) { free(Q0); free(R); return -1.0; }
+#pragma omp parallel for schedule(static)
     for (int k = interior_lo(g, 2); k <= interior_hi(g, 2); ++k)
       for (int j = interior_lo(g, 1); j <= interior_hi(g, 1); ++j)
         for (int i = interior_lo(g, 0); i <= interior_hi(g, 0); ++i) {
