@@ -197,6 +197,14 @@ int jz_profile_end(jz_grid* g);
 int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
 int jz_set_tiling(jz_grid* g, int kc);
 
+/* Stage kernel variant of a JZ_P32 grid: 0 (default) is the scalar kernel;
+ * 1 pairs two nodes per thread and computes them with packed FP32x2
+ * instructions (fewer instructions, but fewer resident warps: slower on the
+ * 256x192x192 workload).  Both evaluate the same formulas; results agree to
+ * FP32 rounding.  JZ_EINVAL for other precisions.  A batch uses its first
+ * grid's variant. */
+int jz_set_stage_variant(jz_grid* g, int variant);
+
 /* --- diagnostics without device allocation --------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * may only use device arrays they were handed -- a plug-in called by a host

@@ -24,6 +24,7 @@ struct GridDev {
   double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
+  int variant;         // stage kernel: 0 scalar, 1 paired FP32x2 (P32 only)
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
 };
@@ -77,8 +78,8 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
 // batched stage: a device table of per-grid stage contexts and work items
 size_t stage_ctx_bytes(int prec);
 void stage_ctx_fill(void* host_dst, const GridDev& g);
-cudaError_t launch_stage_batch(int prec, const void* ctx, const int4* items, int nitems, unsigned int* queue,
-                               int stage, int qsel, int qout, cudaStream_t s);
+cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int4* items, int nitems,
+                               unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s);
 cudaError_t stage_configure();  // one-time kernel attributes (dynamic shared memory)
 
 }  // namespace jz

@@ -1,0 +1,193 @@
+// jz_stage_common.cuh -- pieces shared by the scalar and the paired (FP32x2)
+// fused stage kernels: ring record layout, flow constants in the arithmetic
+// type, elementary-function choices, TMA / mbarrier helpers (inline PTX), the
+// per-grid kernel context and the per-launch stage selection.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "jz_internal.h"
+
+namespace jz {
+namespace stg {
+
+// ring record
+enum { V_RHO = 0, V_U = 1, V_V = 2, V_W = 3, V_E = 4, V_P = 5, V_T = 6, NV = 7 };
+
+template <typename R>
+struct KConst {
+  R gamma, gm1, cp, mu_inf, s1, s1p1, inv_pr, inv_prt, cs2, k2, k4, sigma;
+  int viscous, sgs, sig_half;
+};
+
+template <typename R>
+__host__ __device__ inline KConst<R> make_kconst(const FlowC& F) {
+  KConst<R> c;
+  c.gamma = (R)F.gamma;
+  c.gm1 = (R)F.gm1;
+  c.cp = (R)F.cp;
+  c.mu_inf = (R)F.mu_inf;
+  c.s1 = (R)F.s1;
+  c.s1p1 = (R)(1.0 + F.s1);
+  c.inv_pr = (R)(1.0 / F.pr);
+  c.inv_prt = (R)(1.0 / F.prt);
+  c.cs2 = (R)(F.cs * F.cs);
+  c.k2 = (R)F.k2;
+  c.k4 = (R)F.k4;
+  c.sigma = (R)F.sigma;
+  c.viscous = F.viscous;
+  c.sgs = F.cs > 0.0;
+  c.sig_half = F.sigma == 0.5;
+  return c;
+}
+
+template <typename R>
+__device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+// Elementary functions.  The FP32 kernel uses the hardware approximations
+// (sqrt.approx, rcp.approx, ex2/lg2.approx: a few ulp, far below the FP32
+// error of the scheme itself); the FP64 kernel keeps IEEE operations.
+template <typename R> struct Fn;
+template <> struct Fn<float> {
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
+  // x^e = 2^(e log2 x) for x > 0 (no library call inside the flux code)
+  static __device__ __forceinline__ float powp(float x, float e) {
+    float l, y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    l *= e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+    return y;
+  }
+  // J^(-2/3) = 2^(-2/3 log2 J), J > 0
+  static __device__ __forceinline__ float jm23(float J) {
+    float l, y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(J));
+    l *= -2.0f / 3.0f;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+    return y;
+  }
+};
+template <> struct Fn<double> {
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double powp(double x, double e) { return pow(x, e); }
+  static __device__ __forceinline__ double jm23(double J) {
+    const double cb = cbrt(J);
+    return 1.0 / (cb * cb);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX, sm_90+ async proxy)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM cycles (about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long start = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - start > (1LL << 31)) return false;
+  }
+  return true;
+}
+
+// 4-D tiled TMA load: box at (x, y, z, w) of the tensor map into shared memory.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Everything the stage kernel needs about one grid: TMA maps of the three
+// state copies and of the metrics, layout, state pointers, device scalars
+// (time step), flow constants and the k-chunk length.  Passed as a kernel
+// parameter for one grid, or read from a device table for a batch.
+template <typename R, typename MT>
+struct alignas(64) StageCtx {
+  CUtensorMap tmQ[3];  // Q0, QA, QB
+  CUtensorMap tmM;     // metrics
+  Layout L;
+  R* Q[3];             // Q0, QA, QB
+  const Scalars* sc;
+  int* err;            // sticky error flag (bounded-wait timeout)
+  FlowC F;
+  KConst<R> k;         // flow constants in the arithmetic type, prepared on the host
+  int kc;
+};
+
+// Per-launch stage selection: alpha_l, input copy Q^(l-1), output copy Q^(l).
+struct StageSel {
+  double alpha;
+  int qin, qout;
+};
+
+__device__ __forceinline__ void init_barriers(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// after a timeout: record it and let this CTA's copies still in flight land
+__device__ __forceinline__ void drain_after_timeout(uint64_t* bar, int* err, const int issued[3],
+                                                    const int waited[3]) {
+  if (threadIdx.x == 0) {
+    atomicExch(err, 1);
+    for (int b = 0; b < 3; ++b)
+      for (int u = waited[b]; u < issued[b]; ++u)
+        if (!mbar_wait_bounded(&bar[b], u & 1)) break;  // phase u of barrier b
+  }
+  __syncthreads();
+}
+
+constexpr double kRkAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0};
+
+}  // namespace stg
+
+// paired FP32x2 kernel for P32 (jz_stage_pair.cu)
+cudaError_t stage_pair_configure();
+cudaError_t launch_stage_pair(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);
+cudaError_t launch_stage_pair_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                                    const stg::StageSel& st, cudaStream_t s);
+}  // namespace jz

@@ -80,6 +80,7 @@ def lib() -> C.CDLL:
             "jz_profile_end": ([G], C.c_int),
             "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "jz_set_tiling": ([G, C.c_int], C.c_int),
+            "jz_set_stage_variant": ([G, C.c_int], C.c_int),
         }
         sig["jz_state_diagnostics_static"] = ([C.c_longlong, C.c_int, VP, VP, C.c_double, VP, VP], C.c_int)
         for name, (args, res) in sig.items():
@@ -212,6 +213,10 @@ def jz_get_tiling(h):
 
 def jz_set_tiling(h, kc: int) -> None:
     _check(lib().jz_set_tiling(h, kc))
+
+
+def jz_set_stage_variant(h, variant: int) -> None:
+    _check(lib().jz_set_stage_variant(h, variant))
 
 
 def jz_state_diagnostics_static(n_nodes: int, fp64: bool, q_ptr: int, vol_ptr: int, gamma: float, out_ptr: int,

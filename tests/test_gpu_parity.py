@@ -164,7 +164,8 @@ def test_fp32_modes_error_bound_config0(jz, orc):
     normalised L2 <= 1e-4.  Far-field face nodes are excluded from the max:
     the Riemann condition's upwind and sonic branch choices are discontinuous
     and may fall differently in FP32 and FP64.  P32_M64 gives bitwise the
-    same state as P32 (metrics are consumed in FP32 either way)."""
+    same state as P32's scalar kernel (metrics are consumed in FP32 either
+    way); the paired FP32x2 kernel agrees to FP32 rounding."""
     c = W.config0()
     o = orc.Oracle(c["grid"], c["flow"])
     Q = o.init(c["seed"])
@@ -172,8 +173,9 @@ def test_fp32_modes_error_bound_config0(jz, orc):
     ref = o.inner(Q)
     inner = (slice(3, -3),) * 3
     outs = []
-    for prec in (W.P32_M64, W.P32):
+    for prec, variant in ((W.P32_M64, 0), (W.P32, 0), (W.P32, 1)):
         g = jz.Grid(dict(c["grid"], precision=prec)).init(c["flow"], c["seed"])
+        jz.jz_set_stage_variant(g.h, variant)
         g.nsteps(c["steps"], cfl=c["cfl"])
         got = g.download()
         outs.append(got)
@@ -233,3 +235,24 @@ def test_launch_counter_advances(jz):
     g.nsteps(3, cfl=0.5)
     g.synchronize()
     assert jz.jz_launch_count() - before == 3 * 16  # time step, 5 x (stage + boundary nodes + ghosts)
+
+
+@pytest.mark.parametrize("shape,amp", [((48, 32, 32), 0.0), ((37, 29, 23), 0.05)])
+def test_paired_fp32_kernel_matches_scalar(jz, shape, amp):
+    """The paired FP32x2 stage kernel (an option for P32) and the scalar FP32
+    kernel evaluate the same formulas: after 5 steps the states agree to FP32
+    rounding (interior), including ragged tiles."""
+    grid = W.jet_grid(*shape, map_amp=amp, map_seed=2, precision=W.P32)
+    outs = []
+    for variant in (1, 0):
+        g = jz.Grid(grid).init(W.jet_flow(), 4)
+        jz.jz_set_stage_variant(g.h, variant)
+        g.nsteps(5, cfl=0.5)
+        outs.append(g.download())
+    inner = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
+    a, b = outs[0][inner], outs[1][inner]
+    for v in range(5):
+        assert np.abs(a[v] - b[v]).max() <= 2e-5 * np.abs(b[v]).max() + 1e-6, v
+    with pytest.raises(jz.JzError):
+        g64 = jz.Grid(dict(grid, precision=W.P64)).init(W.jet_flow(), 4)
+        jz.jz_set_stage_variant(g64.h, 1)
