@@ -197,12 +197,15 @@ int jz_profile_end(jz_grid* g);
 int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
 int jz_set_tiling(jz_grid* g, int kc);
 
-/* Stage kernel variant of a JZ_P32 grid: 0 (default) is the scalar kernel;
- * 1 pairs two nodes per thread and computes them with packed FP32x2
- * instructions (fewer instructions, but fewer resident warps: slower on the
- * 256x192x192 workload).  Both evaluate the same formulas; results agree to
- * FP32 rounding.  JZ_EINVAL for other precisions.  A batch uses its first
- * grid's variant. */
+/* Stage kernel variant of a JZ_P32 grid: 2 (default) keeps node records as
+ * float4 + float vectors in shared memory (three block barriers per plane);
+ * 0 is the scalar kernel (one shared-memory value per load, four barriers
+ * per plane); 1 pairs two nodes per thread and computes them with packed
+ * FP32x2 instructions (fewer instructions, but half the resident warps).
+ * All three evaluate the same formulas; results agree to FP32 rounding.
+ * Measured on the 256x192x192 mapped jet (ms per stage): 2: 0.44,
+ * 0: 0.55, 1: 0.61.  JZ_EINVAL for other precisions or variants.  A batch
+ * uses its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
 /* --- diagnostics without device allocation --------------------------------

@@ -246,7 +246,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 4-D map over a field array [fields][k][j][i-row of pitch]: box = one plane of
 // (ti+4) x (tj+4) nodes (tile plus two-node halo) x all fields.  Coordinates
 // outside the array read as zero.
-int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int fields, int prec) {
+int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int fields, int prec, int halo_rows = 2) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   StageTiling t = stage_tiling(prec);
@@ -254,7 +254,7 @@ int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int f
   cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.n[1] + 2 * NG), (cuuint64_t)(L.n[2] + 2 * NG),
                         (cuuint64_t)fields};
   cuuint64_t strides[3] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.npad * es};
-  cuuint32_t box[4] = {(cuuint32_t)(t.ti + 4), (cuuint32_t)(t.tj + 4), 1, (cuuint32_t)fields};
+  cuuint32_t box[4] = {(cuuint32_t)(t.ti + 4), (cuuint32_t)(t.tj + 2 * halo_rows), 1, (cuuint32_t)fields};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -315,7 +315,7 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   d.partial = (double*)(g->base + cv.off_partial);
   d.inflow = (double*)(g->base + cv.off_inflow);
   d.kc = default_kc(cv.L, d.prec);
-  d.variant = 0;  // scalar kernel: measured faster than the paired one on c1 (0.55 vs 0.61 ms per stage)
+  d.variant = d.prec == JZ_P32 ? 2 : 0;  // P32: the vector-record kernel (fastest measured)
   memset(&d.F, 0, sizeof(d.F));
   // coordinate tables
   double* tab = (double*)(g->base + cv.off_tab);
@@ -349,7 +349,8 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   if ((rc = make_plane_map(&d.tmQ[0], d.Q0, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmQ[1], d.QA, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmQ[2], d.QB, st64, cv.L, 5, d.prec)) ||
-      (rc = make_plane_map(&d.tmM, d.M, mt64, cv.L, 10, d.prec))) {
+      (rc = make_plane_map(&d.tmM, d.M, mt64, cv.L, 10, d.prec)) ||
+      (rc = make_plane_map(&d.tmMv, d.M, mt64, cv.L, 10, d.prec, 1))) {
     delete g;
     return rc;
   }
@@ -550,8 +551,8 @@ int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc) {
 
 int jz_set_stage_variant(jz_grid* g, int variant) {
   if (int rc = check_grid(g, false)) return rc;
-  if (variant != 0 && variant != 1) return fail(JZ_EINVAL, "stage variant must be 0 or 1");
-  if (variant == 1 && g->dev.prec != JZ_P32) return fail(JZ_EINVAL, "the paired stage kernel is FP32 (JZ_P32) only");
+  if (variant < 0 || variant > 2) return fail(JZ_EINVAL, "stage variant must be 0, 1 or 2");
+  if (variant != 0 && g->dev.prec != JZ_P32) return fail(JZ_EINVAL, "stage variants 1 and 2 are FP32 (JZ_P32) only");
   g->dev.variant = variant;
   if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
   if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }

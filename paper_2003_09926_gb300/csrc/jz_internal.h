@@ -24,9 +24,10 @@ struct GridDev {
   double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
-  int variant;         // stage kernel: 0 scalar, 1 paired FP32x2 (P32 only)
+  int variant;         // stage kernel of P32: 0 scalar, 1 paired FP32x2, 2 vector records
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
+  CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)
 };
 
 // Interior-vs-shell enumeration: every padded node outside the box [a, b].

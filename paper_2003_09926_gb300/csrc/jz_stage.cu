@@ -564,6 +564,7 @@ void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
   X.tmQ[1] = g.tmQ[1];
   X.tmQ[2] = g.tmQ[2];
   X.tmM = g.tmM;
+  X.tmMv = g.tmMv;
   X.L = g.L;
   X.Q[0] = (R*)g.Q0;
   X.Q[1] = (R*)g.QA;
@@ -623,6 +624,7 @@ cudaError_t stage_configure() {
   if ((e = configure_one<float, double, TIM, TJM>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32>()) != cudaSuccess) return e;
   if ((e = stage_pair_configure()) != cudaSuccess) return e;
+  if ((e = stage_v_configure()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -631,10 +633,11 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
     case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_one<float, double, TIM, TJM>(g, stage, qsel, qout, s);
     default:
-      if (g.variant == 1) {
+      if (g.variant == 1 || g.variant == 2) {
         StageCtx<float, float> X;
         fill_ctx(X, g);
-        return launch_stage_pair(X, StageSel{kRkAlpha[stage], qsel, qout}, s);
+        const StageSel st{kRkAlpha[stage], qsel, qout};
+        return g.variant == 1 ? launch_stage_pair(X, st, s) : launch_stage_v(X, st, s);
       }
       return launch_one<float, float, TI32, TJ32>(g, stage, qsel, qout, s);
   }
@@ -660,6 +663,8 @@ cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int
                                unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
   if (prec == JZ_P32 && variant == 1)
     return launch_stage_pair_batch(ctx, items, nitems, queue, StageSel{kRkAlpha[stage], qsel, qout}, s);
+  if (prec == JZ_P32 && variant == 2)
+    return launch_stage_v_batch(ctx, items, nitems, queue, StageSel{kRkAlpha[stage], qsel, qout}, s);
   switch (prec) {
     case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, s);

@@ -141,9 +141,10 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 // (time step), flow constants and the k-chunk length.  Passed as a kernel
 // parameter for one grid, or read from a device table for a batch.
 template <typename R, typename MT>
-struct alignas(64) StageCtx {
+struct alignas(128) StageCtx {
   CUtensorMap tmQ[3];  // Q0, QA, QB
   CUtensorMap tmM;     // metrics
+  CUtensorMap tmMv;    // metrics, box of the tile plus a one-node halo (FP32 record kernel)
   Layout L;
   R* Q[3];             // Q0, QA, QB
   const Scalars* sc;
@@ -185,6 +186,11 @@ constexpr double kRkAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0}
 
 }  // namespace stg
 
+// FP32 kernel with vector node records (jz_stage_v.cu)
+cudaError_t stage_v_configure();
+cudaError_t launch_stage_v(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);
+cudaError_t launch_stage_v_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                                 const stg::StageSel& st, cudaStream_t s);
 // paired FP32x2 kernel for P32 (jz_stage_pair.cu)
 cudaError_t stage_pair_configure();
 cudaError_t launch_stage_pair(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);

@@ -1,0 +1,598 @@
+// jz_stage_v.cu -- the FP32 fused Runge-Kutta stage kernel with vector node
+// records: residual evaluation and stage update in one pass over HBM.
+//
+// Paper: arXiv 2003.09926, Section 3 and Section 4.2: per Runge-Kutta
+// sub-step, the centred inviscid flux in general curvilinear coordinates, the
+// Turkel-Vatsa anisotropic scalar artificial dissipation (pressure sensor,
+// five-point stencil, Section 4.3), the viscous flux (Stokes stress, Fourier
+// heat flux, Sutherland viscosity) plus a Smagorinsky eddy viscosity, then
+// the update Q^(l) = Q^(0) - alpha_l dt J R(Q^(l-1)) of the 5-stage scheme.
+// The residual is taken in face form, R_n = sum_k (h^k_{n+1/2} - h^k_{n-1/2})
+// with h_{n+1/2} = (G_n + G_{n+1})/2 - d_{n+1/2}, G = E - F the contravariant
+// inviscid minus viscous flux: the paper's central difference plus
+// dissipation, telescoping exactly.
+//
+// Organisation (one CTA per SM, 2.5-D streaming over a 32 x 16 (i, j) tile
+// and a chunk of k-planes):
+//  - TMA stages the conserved variables of one plane (tile plus a two-node
+//    halo) into a planar buffer, and the metric fields of one plane (tile
+//    plus a one-node halo) into a second buffer; waits are bounded;
+//  - each staged plane is converted once into two rings of node records:
+//    conserved (rho, rho u, rho v, rho w | e) over five planes and primitive
+//    (u, v, w, T | p) over four planes, each a float4 plus a float, so that a
+//    node's stencil values arrive with two shared-memory loads;
+//  - one thread per node of the plus-shaped set (tile nodes plus the
+//    one-node i and j halo) forms G^k, the dissipation radius lambda~^k and
+//    the sensor nu^k of its node (tile threads in all three directions, halo
+//    threads in their own direction);
+//  - i and j face fluxes go through shared memory as float4 + float records,
+//    the k face flux of a column stays in its thread's registers;
+//  - three block barriers per plane: node pass | face pass | residual,
+//    k face, update and conversion of the plane three ahead.
+#include <cmath>
+#include <cstdint>
+
+#include "jz_stage_common.cuh"
+
+namespace jz {
+
+using namespace stg;
+
+namespace {
+
+namespace vr {
+constexpr int TI = 32, TJ = 16;
+constexpr int NTILE = TI * TJ;                  // 512 tile nodes
+constexpr int NJH = 2 * TI, NIH = 2 * TJ;       // j-halo (rows -1, TJ) and i-halo (columns -1, TI) nodes
+constexpr int NT = NTILE + NJH + NIH;           // 608 threads
+constexpr int RW = TI + 4, RH = TJ + 4, PL = RW * RH;  // staged plane: tile + two-node halo (36 x 20)
+constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 36 columns
+constexpr int NQS = 5, NPS = 4;                 // ring depths (planes)
+constexpr int GIW = TI + 2, GJH = TJ + 2;       // node buffers: columns -1..TI / rows -1..TJ
+constexpr int HIW = TI + 1, HJH = TJ + 1;       // face buffers
+constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
+constexpr size_t RAW_B = al(4 * 5 * PL);
+constexpr size_t QV_B = al(16 * NQS * PL), QE_B = al(4 * NQS * PL);
+constexpr size_t PV_B = al(16 * NPS * PL), PP_B = al(4 * NPS * PL);
+constexpr size_t MET_B = al(4 * 10 * MPL);
+constexpr size_t GI4_B = al(16 * TJ * GIW), GI1_B = al(4 * TJ * GIW);
+constexpr size_t GJ4_B = al(16 * GJH * TI), GJ1_B = al(4 * GJH * TI);
+constexpr size_t LI_B = al(8 * TJ * GIW), LJ_B = al(8 * GJH * TI);
+constexpr size_t HI4_B = al(16 * TJ * HIW), HI1_B = al(4 * TJ * HIW);
+constexpr size_t HJ4_B = al(16 * HJH * TI), HJ1_B = al(4 * HJH * TI);
+constexpr size_t O_RAW = 0;
+constexpr size_t O_QV = O_RAW + RAW_B;
+constexpr size_t O_QE = O_QV + QV_B;
+constexpr size_t O_PV = O_QE + QE_B;
+constexpr size_t O_PP = O_PV + PV_B;
+constexpr size_t O_MET = O_PP + PP_B;
+constexpr size_t O_GI4 = O_MET + MET_B;
+constexpr size_t O_GI1 = O_GI4 + GI4_B;
+constexpr size_t O_GJ4 = O_GI1 + GI1_B;
+constexpr size_t O_GJ1 = O_GJ4 + GJ4_B;
+constexpr size_t O_LI = O_GJ1 + GJ1_B;
+constexpr size_t O_LJ = O_LI + LI_B;
+constexpr size_t O_HI4 = O_LJ + LJ_B;
+constexpr size_t O_HI1 = O_HI4 + HI4_B;
+constexpr size_t O_HJ4 = O_HI1 + HI1_B;
+constexpr size_t O_HJ1 = O_HJ4 + HJ4_B;
+constexpr size_t O_BAR = O_HJ1 + HJ1_B;
+constexpr size_t BYTES = O_BAR + 128;
+// during a chunk's prologue three more raw planes are staged over the node
+// and face buffers, which are not in use yet
+constexpr size_t O_SCR = O_GI4;
+static_assert(O_BAR - O_SCR >= 3 * RAW_B, "prologue staging does not fit");
+static_assert(BYTES <= 232448, "shared memory");
+constexpr uint32_t RAW_TX = 4 * 5 * PL;
+constexpr uint32_t MET_TX = 4 * 10 * MPL;
+// mbarriers: 0 raw buffer, 1..3 prologue staging, 4 metrics
+constexpr int B_RAW = 0, B_MET = 4, NBAR = 5;
+}  // namespace vr
+
+__device__ __forceinline__ void ld5(const float4* v4, const float* v1, int i, float q[5]) {
+  const float4 a = v4[i];
+  q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+  q[4] = v1[i];
+}
+__device__ __forceinline__ void st5(float4* v4, float* v1, int i, const float q[5]) {
+  v4[i] = make_float4(q[0], q[1], q[2], q[3]);
+  v1[i] = q[4];
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// bounded wait with a fast path (the copy has normally landed long before)
+__device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity) {
+  return mbar_try_wait(bar, parity) || mbar_wait_bounded(bar, parity);
+}
+
+// Node quantities of node (x, y) of plane kk: G^k = E^k - F^k, lambda~^k,
+// nu^k.  Primitive records of the planes below / at / above in slots sM, sC,
+// sP; the conserved record of the plane in slot qC.  DIR = 0: all three
+// directions; DIR = 1 / 2: direction i / j only.
+template <int DIR>
+__device__ __forceinline__ void node_v(const float4* __restrict__ PV, const float* __restrict__ PP,
+                                       const float4* __restrict__ QV, const float* __restrict__ QE,
+                                       const float* __restrict__ met, int sM, int sC, int sP, int qC, int x, int y,
+                                       const KConst<float>& c, float G[3][5], float lt[3], float nu[3], float& Jn) {
+  using namespace vr;
+  const int o = (y + 2) * RW + x + 2;
+  const int mo = (y + 1) * RW + x + 2;
+  float S[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) S[f] = met[f * MPL + mo];
+  Jn = met[9 * MPL + mo];
+  const float4* pc = PV + sC * PL;
+  const float4 r0 = pc[o];
+  const float u = r0.x, v = r0.y, w = r0.z, T = r0.w;
+  const float p = PP[sC * PL + o];
+  const float rho = QV[qC * PL + o].x;
+  const float e = QE[qC * PL + o];
+  constexpr int K0 = DIR == 0 ? 0 : DIR - 1;
+  constexpr int K1 = DIR == 0 ? 3 : DIR;
+
+  float Fv[3][4];  // viscous flux vectors F_m (m = x, y, z), components 1..4
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fv[m][q] = 0.f;
+  if (c.viscous) {
+    // Cartesian gradients of u, v, w, T: J/2 sum_k S^k_m (phi_+ - phi_-)
+    const float4 a0 = pc[o + 1], b0 = pc[o - 1], a1 = pc[o + RW], b1 = pc[o - RW];
+    const float4 a2 = PV[sP * PL + o], b2 = PV[sM * PL + o];
+    const float d0[4] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z, a0.w - b0.w};
+    const float d1[4] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z, a1.w - b1.w};
+    const float d2[4] = {a2.x - b2.x, a2.y - b2.y, a2.z - b2.z, a2.w - b2.w};
+    const float hJ = 0.5f * Jn;
+    float g[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) g[q][m] = hJ * (S[m] * d0[q] + S[3 + m] * d1[q] + S[6 + m] * d2[q]);
+    const float mu = Fn<float>::div(c.mu_inf * T * Fn<float>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
+    float mu_t = 0.f;
+    if (c.sgs) {  // Smagorinsky: rho (C_s Delta)^2 |S|, Delta = J^(-1/3), |S| = sqrt(2 S_ij S_ij)
+      const float s12 = 0.5f * (g[0][1] + g[1][0]), s13 = 0.5f * (g[0][2] + g[2][0]);
+      const float s23 = 0.5f * (g[1][2] + g[2][1]);
+      const float ss =
+          g[0][0] * g[0][0] + g[1][1] * g[1][1] + g[2][2] * g[2][2] + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
+      mu_t = rho * c.cs2 * Fn<float>::sqrt_(2.f * ss) * Fn<float>::jm23(Jn);
+    }
+    const float mue = mu + mu_t;
+    const float kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
+    const float div3 = (g[0][0] + g[1][1] + g[2][2]) * (2.f / 3.f);
+    const float t01 = mue * (g[0][1] + g[1][0]), t02 = mue * (g[0][2] + g[2][0]), t12 = mue * (g[1][2] + g[2][1]);
+    Fv[0][0] = mue * (2.f * g[0][0] - div3); Fv[0][1] = t01; Fv[0][2] = t02;
+    Fv[1][0] = t01; Fv[1][1] = mue * (2.f * g[1][1] - div3); Fv[1][2] = t12;
+    Fv[2][0] = t02; Fv[2][1] = t12; Fv[2][2] = mue * (2.f * g[2][2] - div3);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) Fv[m][3] = u * Fv[m][0] + v * Fv[m][1] + w * Fv[m][2] + kap * g[3][m];
+  }
+
+  float lam[3], U[3];
+  const float cson = Fn<float>::sqrt_(T);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    U[k] = S[3 * k] * u + S[3 * k + 1] * v + S[3 * k + 2] * w;
+    const float sn = Fn<float>::sqrt_(S[3 * k] * S[3 * k] + S[3 * k + 1] * S[3 * k + 1] + S[3 * k + 2] * S[3 * k + 2]);
+    lam[k] = fabsf(U[k]) + cson * sn;
+  }
+  float sq[3] = {0.f, 0.f, 0.f};
+  if (c.sig_half) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sq[k] = Fn<float>::sqrt_(lam[k]);
+  }
+  const float m1 = rho * u, m2 = rho * v, m3 = rho * w;
+#pragma unroll
+  for (int k = K0; k < K1; ++k) {
+    const float Sx = S[3 * k], Sy = S[3 * k + 1], Sz = S[3 * k + 2];
+    float Fk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fk[q] = Sx * Fv[0][q] + Sy * Fv[1][q] + Sz * Fv[2][q];
+    // E^k = [rho U, rho u U + S_x p, rho v U + S_y p, rho w U + S_z p, (e + p) U]
+    G[k][0] = rho * U[k];
+    G[k][1] = m1 * U[k] + Sx * p - Fk[0];
+    G[k][2] = m2 * U[k] + Sy * p - Fk[1];
+    G[k][3] = m3 * U[k] + Sz * p - Fk[2];
+    G[k][4] = (e + p) * U[k] - Fk[3];
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    if (c.sig_half)  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
+      lt[k] = lam[k] + sq[k] * (sq[a] + sq[b]);
+    else
+      lt[k] = lam[k] * (1.f + Fn<float>::powp(Fn<float>::div(lam[a], lam[k]), c.sigma) +
+                        Fn<float>::powp(Fn<float>::div(lam[b], lam[k]), c.sigma));
+    float pm, pp;
+    if (k == 0) { pm = PP[sC * PL + o - 1]; pp = PP[sC * PL + o + 1]; }
+    else if (k == 1) { pm = PP[sC * PL + o - RW]; pp = PP[sC * PL + o + RW]; }
+    else { pm = PP[sM * PL + o]; pp = PP[sP * PL + o]; }
+    nu[k] = Fn<float>::div(fabsf(pp - 2.f * p + pm), pp + 2.f * p + pm);
+  }
+}
+
+// dissipative face flux between nodes a and b of a line m, a, b, p:
+// h = (Ga + Gb)/2 - lam [e2 (qb - qa) - e4 (qp - 3 qb + 3 qa - qm)],
+// lam = (lt_a + lt_b)/2, e2 = k2 max(nu_a, nu_b), e4 = max(0, k4 - e2)
+__device__ __forceinline__ void face_v(const KConst<float>& c, float2 La, float2 Lb, const float Ga[5],
+                                       const float Gb[5], const float qm[5], const float qa[5], const float qb[5],
+                                       const float qp[5], float h[5]) {
+  const float lam = 0.5f * (La.x + Lb.x);
+  const float e2 = c.k2 * fmaxf(La.y, Lb.y);
+  const float e4 = fmaxf(0.f, c.k4 - e2);
+  const float l2 = lam * e2, l4 = lam * e4;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const float d1 = qb[v] - qa[v];
+    const float d3 = (qp[v] - qm[v]) - 3.f * d1;
+    h[v] = 0.5f * (Ga[v] + Gb[v]) - (l2 * d1 - l4 * d3);
+  }
+}
+
+struct Smem {
+  float* raw;
+  float4* QV;
+  float* QE;
+  float4* PV;
+  float* PP;
+  float* met;
+  float4 *Gi4, *Gj4, *Hi4, *Hj4;
+  float *Gi1, *Gj1, *Hi1, *Hj1;
+  float2 *Li, *Lj;
+  uint64_t* bar;
+  __device__ explicit Smem(unsigned char* s) {
+    using namespace vr;
+    raw = reinterpret_cast<float*>(s + O_RAW);
+    QV = reinterpret_cast<float4*>(s + O_QV);
+    QE = reinterpret_cast<float*>(s + O_QE);
+    PV = reinterpret_cast<float4*>(s + O_PV);
+    PP = reinterpret_cast<float*>(s + O_PP);
+    met = reinterpret_cast<float*>(s + O_MET);
+    Gi4 = reinterpret_cast<float4*>(s + O_GI4);
+    Gi1 = reinterpret_cast<float*>(s + O_GI1);
+    Gj4 = reinterpret_cast<float4*>(s + O_GJ4);
+    Gj1 = reinterpret_cast<float*>(s + O_GJ1);
+    Li = reinterpret_cast<float2*>(s + O_LI);
+    Lj = reinterpret_cast<float2*>(s + O_LJ);
+    Hi4 = reinterpret_cast<float4*>(s + O_HI4);
+    Hi1 = reinterpret_cast<float*>(s + O_HI1);
+    Hj4 = reinterpret_cast<float4*>(s + O_HJ4);
+    Hj1 = reinterpret_cast<float*>(s + O_HJ1);
+    bar = reinterpret_cast<uint64_t*>(s + O_BAR);
+  }
+};
+
+// One work item: tile (bx, by), k-chunk bz of grid X, stage st.  The CTA's
+// mbarriers are (re)initialised at the start of every item, so the parity of
+// every wait follows from the plane index.  On a bounded-wait timeout the
+// item records where it gave up, lets its copies in flight land and returns
+// false.
+__device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const StageSel& st, int bx, int by, int bz,
+                                       unsigned char* smem, bool first) {
+  using namespace vr;
+  Smem sm(smem);
+  const Layout& L = X.L;
+  const KConst<float> c = X.k;
+  const int tid = threadIdx.x;
+  const int i0 = bx * TI, j0 = by * TJ;
+  const int t0 = L.lo[2] + bz * X.kc;
+  const int t1 = min(t0 + X.kc, L.hi[2] + 1);
+  const int pbase = t0 - 2;  // first staged plane
+
+  // node role: tile node, j-halo node (rows -1, TJ) or i-halo node (columns -1, TI)
+  int nx, ny, role;
+  if (tid < NTILE) { role = 0; nx = tid % TI; ny = tid / TI; }
+  else if (tid < NTILE + NJH) { role = 2; const int h = tid - NTILE; nx = h % TI; ny = (h / TI) ? TJ : -1; }
+  else { role = 1; const int h = tid - NTILE - NJH; ny = h % TJ; nx = (h / TJ) ? TI : -1; }
+  const int gi = i0 + nx, gj = j0 + ny;
+  const bool own = role == 0 && gi >= L.lo[0] && gi <= L.hi[0] && gj >= L.lo[1] && gj <= L.hi[1];
+
+  // (re)initialise the barriers; every copy of the previous item has been
+  // waited for, and every thread is past its last wait
+  __syncthreads();
+  if (tid == 0) {
+    for (int b = 0; b < NBAR; ++b) {
+      if (!first) mbar_inval(&sm.bar[b]);
+      mbar_init(&sm.bar[b], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // generic-proxy writes to the buffers the prologue stages into, then the barrier
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+
+  // parities: the raw buffer takes plane t0-2, then t0+2, t0+3, ...; the
+  // metric buffer planes t0-1, t0, ...
+  auto raw_parity = [&](int p) { return (uint32_t)((p - t0 - 1) & 1); };
+  auto met_parity = [&](int p) { return (uint32_t)((p - t0 + 1) & 1); };
+  // thread 0's record of copies in flight: bit b of pend = barrier b has an
+  // unwaited copy, bit b of ppar = the parity of that copy's phase
+  uint32_t pend = 0, ppar = 0;
+  auto issue_raw = [&](int p, int b, float* dst, uint32_t parity) {
+    if (tid == 0) {
+      pend |= 1u << b;
+      ppar = (ppar & ~(1u << b)) | (parity << b);
+      fence_async_shared();
+      mbar_expect_tx(&sm.bar[b], RAW_TX);
+      tma_load_4d(dst, &X.tmQ[st.qin], &sm.bar[b], i0, j0, p + NG, 0);
+    }
+  };
+  auto issue_met = [&](int p) {
+    if (tid == 0) {
+      pend |= 1u << B_MET;
+      ppar = (ppar & ~(1u << B_MET)) | ((uint32_t)((p - t0 + 1) & 1) << B_MET);
+      fence_async_shared();
+      mbar_expect_tx(&sm.bar[B_MET], MET_TX);
+      tma_load_4d(sm.met, &X.tmMv, &sm.bar[B_MET], i0, j0 + 1, p + NG, 0);
+    }
+  };
+  bool ok = true;
+  auto wait = [&](int b, uint32_t parity, int p) {
+    const bool r = wait_v(&sm.bar[b], parity);
+    if (tid == 0) {
+      if (r) pend &= ~(1u << b);
+      else if (atomicCAS(X.err, 0, 1) == 0) {
+        int* info = X.err + 1;
+        info[0] = b; info[1] = (int)parity; info[2] = p; info[3] = bx; info[4] = by; info[5] = bz; info[6] = st.qin;
+      }
+    }
+    ok = ok && r;
+  };
+  auto qslot = [&](int p) { return (p - pbase) % NQS; };
+  auto pslot = [&](int p) { return (p - pbase) & (NPS - 1); };
+
+  // convert staged plane p (planar, in src) into the ring records
+  auto convert = [&](const float* src, int p) {
+    float4* qv = sm.QV + qslot(p) * PL;
+    float* qe = sm.QE + qslot(p) * PL;
+    float4* pv = sm.PV + pslot(p) * PL;
+    float* pp = sm.PP + pslot(p) * PL;
+    // halo threads (lighter elsewhere) take the second round first
+    for (int e = (tid + NJH + NIH) % NT; e < PL; e += NT) {
+      const float q0 = src[e], q1 = src[PL + e], q2 = src[2 * PL + e], q3 = src[3 * PL + e], q4 = src[4 * PL + e];
+      const float ri = Fn<float>::rcp(q0);
+      const float u = q1 * ri, v = q2 * ri, w = q3 * ri;
+      const float pr = c.gm1 * (q4 - 0.5f * q0 * (u * u + v * v + w * w));
+      qv[e] = make_float4(q0, q1, q2, q3);
+      qe[e] = q4;
+      pv[e] = make_float4(u, v, w, c.gamma * pr * ri);
+      pp[e] = pr;
+    }
+  };
+
+  // node pass for plane kk: i/j node data to shared memory, k data returned
+  auto node_pass = [&](int kk, float G3[5], float& lt3, float& nu3, float& Jn) {
+    const int sM = pslot(kk - 1), sC = pslot(kk), sP = pslot(kk + 1), qC = qslot(kk);
+    float G[3][5], lt[3], nu[3];
+    if (role == 0) {
+      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jn);
+      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, G[0]);
+      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, G[1]);
+      sm.Li[ny * GIW + nx + 1] = make_float2(lt[0], nu[0]);
+      sm.Lj[(ny + 1) * TI + nx] = make_float2(lt[1], nu[1]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) G3[v] = G[2][v];
+      lt3 = lt[2];
+      nu3 = nu[2];
+    } else if (role == 1) {
+      float Jh;
+      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
+      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, G[0]);
+      sm.Li[ny * GIW + nx + 1] = make_float2(lt[0], nu[0]);
+    } else {
+      float Jh;
+      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
+      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, G[1]);
+      sm.Lj[(ny + 1) * TI + nx] = make_float2(lt[1], nu[1]);
+    }
+  };
+
+  // i/j face fluxes of plane kk
+  auto face_pass = [&](int kk) {
+    const float4* qv = sm.QV + qslot(kk) * PL;
+    const float* qe = sm.QE + qslot(kk) * PL;
+    auto iface = [&](int x, int y) {  // face between x-1 and x in row y
+      float Ga[5], Gb[5], q[4][5], h[5];
+      ld5(sm.Gi4, sm.Gi1, y * GIW + x, Ga);
+      ld5(sm.Gi4, sm.Gi1, y * GIW + x + 1, Gb);
+      const int base = (y + 2) * RW + x;  // node x-2
+#pragma unroll
+      for (int n = 0; n < 4; ++n) ld5(qv, qe, base + n, q[n]);
+      face_v(c, sm.Li[y * GIW + x], sm.Li[y * GIW + x + 1], Ga, Gb, q[0], q[1], q[2], q[3], h);
+      st5(sm.Hi4, sm.Hi1, y * HIW + x, h);
+    };
+    auto jface = [&](int x, int y) {  // face between y-1 and y in column x
+      float Ga[5], Gb[5], q[4][5], h[5];
+      ld5(sm.Gj4, sm.Gj1, y * TI + x, Ga);
+      ld5(sm.Gj4, sm.Gj1, (y + 1) * TI + x, Gb);
+      const int base = y * RW + x + 2;  // node y-2
+#pragma unroll
+      for (int n = 0; n < 4; ++n) ld5(qv, qe, base + n * RW, q[n]);
+      face_v(c, sm.Lj[y * TI + x], sm.Lj[(y + 1) * TI + x], Ga, Gb, q[0], q[1], q[2], q[3], h);
+      st5(sm.Hj4, sm.Hj1, y * TI + x, h);
+    };
+    if (role == 0) {
+      iface(nx, ny);
+      jface(nx, ny);
+    } else {
+      const int h = tid - NTILE;  // the last i-face of each row and j-face of each column
+      if (h < TJ) iface(TI, h);
+      else if (h < TJ + TI) jface(h - TJ, TJ);
+    }
+  };
+
+  // i/j residual of this thread's tile node
+  auto rij = [&](float R[5]) {
+    float a[5], b[5], cc[5], d[5];
+    ld5(sm.Hi4, sm.Hi1, ny * HIW + nx + 1, a);
+    ld5(sm.Hi4, sm.Hi1, ny * HIW + nx, b);
+    ld5(sm.Hj4, sm.Hj1, (ny + 1) * TI + nx, cc);
+    ld5(sm.Hj4, sm.Hj1, ny * TI + nx, d);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) R[v] = (a[v] - b[v]) + (cc[v] - d[v]);
+  };
+
+  // k face flux between planes ka and ka+1 of this thread's column
+  auto kface = [&](int ka, const float Ga[5], const float Gb[5], float lta, float ltb, float nua, float nub,
+                   float h[5]) {
+    const int o = (ny + 2) * RW + nx + 2;
+    float q[4][5];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int s = qslot(ka - 1 + n);
+      ld5(sm.QV + s * PL, sm.QE + s * PL, o, q[n]);
+    }
+    face_v(c, make_float2(lta, nua), make_float2(ltb, nub), Ga, Gb, q[0], q[1], q[2], q[3], h);
+  };
+
+  const float adt = (float)(st.alpha * X.sc->dt);
+  const long long npad = L.npad;
+  float* const Qo = X.Q[st.qout];
+  const float* const Q0 = X.Q[0];
+  float* scr[3] = {reinterpret_cast<float*>(smem + O_SCR), reinterpret_cast<float*>(smem + O_SCR + RAW_B),
+                   reinterpret_cast<float*>(smem + O_SCR + 2 * RAW_B)};
+
+  // ---- prologue: planes t0-2 .. t0+1 staged at once, converted
+  issue_raw(t0 - 2, B_RAW, sm.raw, 0);
+  issue_raw(t0 - 1, 1, scr[0], 0);
+  issue_raw(t0, 2, scr[1], 0);
+  issue_raw(t0 + 1, 3, scr[2], 0);
+  issue_met(t0 - 1);
+  wait(B_RAW, 0, t0 - 2);
+  convert(sm.raw, t0 - 2);
+  wait(1, 0, t0 - 1);
+  convert(scr[0], t0 - 1);
+  wait(2, 0, t0);
+  convert(scr[1], t0);
+  wait(3, 0, t0 + 1);
+  convert(scr[2], t0 + 1);
+  if (__syncthreads_or(!ok)) goto fail;
+  issue_raw(t0 + 2, B_RAW, sm.raw, raw_parity(t0 + 2));
+
+  {
+    float G3m[5], lt3m = 0.f, nu3m = 0.f, Jm = 0.f;
+    float G3c[5], lt3c = 0.f, nu3c = 0.f, Jc = 0.f;
+    float Rc[5], hprev[5];
+    wait(B_MET, met_parity(t0 - 1), t0 - 1);
+    node_pass(t0 - 1, G3m, lt3m, nu3m, Jm);
+    if (__syncthreads_or(!ok)) goto fail;
+    issue_met(t0);
+    wait(B_MET, met_parity(t0), t0);
+    node_pass(t0, G3c, lt3c, nu3c, Jc);
+    if (__syncthreads_or(!ok)) goto fail;
+    issue_met(t0 + 1);
+    face_pass(t0);
+    __syncthreads();
+    if (role == 0) {
+      rij(Rc);
+      kface(t0 - 1, G3m, G3c, lt3m, lt3c, nu3m, nu3c, hprev);
+    }
+    wait(B_RAW, raw_parity(t0 + 2), t0 + 2);
+    convert(sm.raw, t0 + 2);
+    if (__syncthreads_or(!ok)) goto fail;
+    if (t0 + 3 <= t1 + 1) issue_raw(t0 + 3, B_RAW, sm.raw, raw_parity(t0 + 3));
+
+    // ---- march in k: iteration t writes plane t
+    for (int t = t0; t < t1; ++t) {
+      float G3n[5], lt3n = 0.f, nu3n = 0.f, Jn = 0.f;
+      wait(B_MET, met_parity(t + 1), t + 1);
+      node_pass(t + 1, G3n, lt3n, nu3n, Jn);
+      if (__syncthreads_or(!ok)) goto fail;
+      if (t + 2 <= t1) issue_met(t + 2);
+      float q0[5];
+      long long n = 0;
+      if (own) {
+        n = L.at(gi, gj, t);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q0[v] = Q0[v * npad + n];
+      }
+      face_pass(t + 1);
+      __syncthreads();
+      if (role == 0) {
+        float Rn[5], hk[5];
+        rij(Rn);
+        kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, hk);
+        if (own) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          G3c[v] = G3n[v];
+          Rc[v] = Rn[v];
+          hprev[v] = hk[v];
+        }
+        lt3c = lt3n;
+        nu3c = nu3n;
+        Jc = Jn;
+      }
+      if (t + 3 <= t1 + 1) {
+        wait(B_RAW, raw_parity(t + 3), t + 3);
+        convert(sm.raw, t + 3);
+      }
+      if (__syncthreads_or(!ok)) goto fail;
+      if (t + 4 <= t1 + 1) issue_raw(t + 4, B_RAW, sm.raw, raw_parity(t + 4));
+    }
+  }
+  return true;
+
+fail:
+  // let this item's copies in flight land before the shared memory is reused
+  if (tid == 0) {
+    atomicExch(X.err, 1);
+    for (int b = 0; b < NBAR; ++b)
+      if (pend & (1u << b)) mbar_wait_bounded(&sm.bar[b], (ppar >> b) & 1u);
+  }
+  __syncthreads();
+  return false;
+}
+
+__global__ void __launch_bounds__(vr::NT, 1) k_stage_v(const __grid_constant__ StageCtx<float, float> X, const StageSel st) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  item_v(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true);
+}
+
+__global__ void __launch_bounds__(vr::NT, 1)
+    k_stage_v_batch(const StageCtx<float, float>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
+                    unsigned int* queue, const StageSel st) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int next;
+  bool first = true;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int it = next;
+    __syncthreads();
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    if (!item_v(ctx[w.x], st, w.y, w.z, w.w, smem, first)) break;
+    first = false;
+  }
+}
+
+}  // namespace
+
+cudaError_t stage_v_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_stage_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage_v_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
+}
+
+cudaError_t launch_stage_v(const StageCtx<float, float>& X, const StageSel& st, cudaStream_t s) {
+  const Layout& L = X.L;
+  const int nz = L.hi[2] - L.lo[2] + 1;
+  dim3 grid((L.hi[0] + vr::TI) / vr::TI, (L.hi[1] + vr::TJ) / vr::TJ, (nz + X.kc - 1) / X.kc);
+  k_stage_v<<<grid, vr::NT, vr::BYTES, s>>>(X, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_v_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                                 const StageSel& st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  const int ctas = nitems < 152 ? nitems : 152;
+  k_stage_v_batch<<<ctas, vr::NT, vr::BYTES, s>>>((const StageCtx<float, float>*)ctx, items, nitems, queue, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace jz

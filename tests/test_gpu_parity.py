@@ -165,7 +165,7 @@ def test_fp32_modes_error_bound_config0(jz, orc):
     the Riemann condition's upwind and sonic branch choices are discontinuous
     and may fall differently in FP32 and FP64.  P32_M64 gives bitwise the
     same state as P32's scalar kernel (metrics are consumed in FP32 either
-    way); the paired FP32x2 kernel agrees to FP32 rounding."""
+    way); the paired FP32x2 and vector-record kernels agree to FP32 rounding."""
     c = W.config0()
     o = orc.Oracle(c["grid"], c["flow"])
     Q = o.init(c["seed"])
@@ -173,7 +173,7 @@ def test_fp32_modes_error_bound_config0(jz, orc):
     ref = o.inner(Q)
     inner = (slice(3, -3),) * 3
     outs = []
-    for prec, variant in ((W.P32_M64, 0), (W.P32, 0), (W.P32, 1)):
+    for prec, variant in ((W.P32_M64, 0), (W.P32, 0), (W.P32, 1), (W.P32, 2)):
         g = jz.Grid(dict(c["grid"], precision=prec)).init(c["flow"], c["seed"])
         jz.jz_set_stage_variant(g.h, variant)
         g.nsteps(c["steps"], cfl=c["cfl"])
@@ -237,16 +237,41 @@ def test_launch_counter_advances(jz):
     assert jz.jz_launch_count() - before == 3 * 16  # time step, 5 x (stage + boundary nodes + ghosts)
 
 
-@pytest.mark.parametrize("shape,amp", [((48, 32, 32), 0.0), ((37, 29, 23), 0.05)])
-def test_paired_fp32_kernel_matches_scalar(jz, shape, amp):
-    """The paired FP32x2 stage kernel (an option for P32) and the scalar FP32
-    kernel evaluate the same formulas: after 5 steps the states agree to FP32
-    rounding (interior), including ragged tiles."""
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("nk", [1, 12])
+def test_fp32_kernel_variants_periodic(jz, variant, nk):
+    """Periodic, mapped, viscous grid (staged planes wrap through the ghost
+    layers, including a single-plane periodic direction): the other FP32
+    kernels agree with the scalar FP32 kernel to FP32 rounding after 5 steps
+    at a fixed time step."""
+    grid = W.periodic_grid(40, 20, nk, hi=(2.0, 1.5, 1.2), map_amp=0.3, map_seed=5, precision=W.P32)
+    Qin = W.random_state((nk, 20, 40), seed=7)
+    outs = []
+    for var in (variant, 0):
+        g = jz.Grid(grid).init(W.jet_flow(re=2e3), 0)
+        g.upload(Qin)
+        jz.jz_set_stage_variant(g.h, var)
+        g.nsteps(5, dt=2e-4)
+        outs.append(g.download())
+    for v in range(5):
+        assert np.abs(outs[0][v] - outs[1][v]).max() <= 2e-5 * np.abs(outs[1][v]).max() + 1e-6, v
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("shape,amp,kc", [((48, 32, 32), 0.0, None), ((37, 29, 23), 0.05, None),
+                                          ((37, 29, 23), 0.05, 1), ((40, 20, 33), 0.03, 4)])
+def test_fp32_kernel_variants_match_scalar(jz, variant, shape, amp, kc):
+    """The other FP32 stage kernels (1: paired FP32x2, 2: vector node records)
+    and the scalar FP32 kernel evaluate the same formulas: after 5 steps the
+    states agree to FP32 rounding (interior), including ragged tiles and
+    k-chunks of one and of four planes."""
     grid = W.jet_grid(*shape, map_amp=amp, map_seed=2, precision=W.P32)
     outs = []
-    for variant in (1, 0):
+    for var in (variant, 0):
         g = jz.Grid(grid).init(W.jet_flow(), 4)
-        jz.jz_set_stage_variant(g.h, variant)
+        jz.jz_set_stage_variant(g.h, var)
+        if kc is not None:
+            jz.jz_set_tiling(g.h, kc)
         g.nsteps(5, cfl=0.5)
         outs.append(g.download())
     inner = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
@@ -255,4 +280,4 @@ def test_paired_fp32_kernel_matches_scalar(jz, shape, amp):
         assert np.abs(a[v] - b[v]).max() <= 2e-5 * np.abs(b[v]).max() + 1e-6, v
     with pytest.raises(jz.JzError):
         g64 = jz.Grid(dict(grid, precision=W.P64)).init(W.jet_flow(), 4)
-        jz.jz_set_stage_variant(g64.h, 1)
+        jz.jz_set_stage_variant(g64.h, variant)
