@@ -350,7 +350,8 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
       (rc = make_plane_map(&d.tmQ[1], d.QA, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmQ[2], d.QB, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmM, d.M, mt64, cv.L, 10, d.prec)) ||
-      (rc = make_plane_map(&d.tmMv, d.M, mt64, cv.L, 10, d.prec, 1))) {
+      (rc = make_plane_map(&d.tmMv, d.M, mt64, cv.L, 10, d.prec, 1)) ||
+      (rc = make_plane_map(&d.tmQ0u, d.Q0, st64, cv.L, 5, d.prec, 0))) {
     delete g;
     return rc;
   }

@@ -28,6 +28,7 @@ struct GridDev {
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
   CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)
+  CUtensorMap tmQ0u;   // Q0, box of the tile rows only (P32)
 };
 
 // Interior-vs-shell enumeration: every padded node outside the box [a, b].

@@ -565,6 +565,7 @@ void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
   X.tmQ[2] = g.tmQ[2];
   X.tmM = g.tmM;
   X.tmMv = g.tmMv;
+  X.tmQ0u = g.tmQ0u;
   X.L = g.L;
   X.Q[0] = (R*)g.Q0;
   X.Q[1] = (R*)g.QA;

@@ -145,6 +145,7 @@ struct alignas(128) StageCtx {
   CUtensorMap tmQ[3];  // Q0, QA, QB
   CUtensorMap tmM;     // metrics
   CUtensorMap tmMv;    // metrics, box of the tile plus a one-node halo (FP32 record kernel)
+  CUtensorMap tmQ0u;   // Q0, box of the tile rows (FP32 record kernel's update)
   Layout L;
   R* Q[3];             // Q0, QA, QB
   const Scalars* sc;

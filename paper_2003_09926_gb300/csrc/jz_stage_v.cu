@@ -18,17 +18,17 @@
 //    halo) into a planar buffer, and the metric fields of one plane (tile
 //    plus a one-node halo) into a second buffer; waits are bounded;
 //  - each staged plane is converted once into two rings of node records:
-//    conserved (rho, rho u, rho v, rho w | e) over five planes and primitive
-//    (u, v, w, T | p) over four planes, each a float4 plus a float, so that a
-//    node's stencil values arrive with two shared-memory loads;
+//    conserved (rho, rho u, rho v, rho w | e) and primitive (u, v, w, T | p),
+//    each a float4 plus a float over four planes, so that a node's stencil
+//    values arrive with two shared-memory loads;
 //  - one thread per node of the plus-shaped set (tile nodes plus the
 //    one-node i and j halo) forms G^k, the dissipation radius lambda~^k and
 //    the sensor nu^k of its node (tile threads in all three directions, halo
 //    threads in their own direction);
 //  - i and j face fluxes go through shared memory as float4 + float records,
 //    the k face flux of a column stays in its thread's registers;
-//  - three block barriers per plane: node pass | face pass | residual,
-//    k face, update and conversion of the plane three ahead.
+//  - three block barriers per plane: node pass | i, j and k face fluxes |
+//    residual, update and conversion of the plane three ahead.
 #include <cmath>
 #include <cstdint>
 
@@ -47,14 +47,19 @@ constexpr int NJH = 2 * TI, NIH = 2 * TJ;       // j-halo (rows -1, TJ) and i-ha
 constexpr int NT = NTILE + NJH + NIH;           // 608 threads
 constexpr int RW = TI + 4, RH = TJ + 4, PL = RW * RH;  // staged plane: tile + two-node halo (36 x 20)
 constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 36 columns
-constexpr int NQS = 5, NPS = 4;                 // ring depths (planes)
-constexpr int GIW = TI + 2, GJH = TJ + 2;       // node buffers: columns -1..TI / rows -1..TJ
-constexpr int HIW = TI + 1, HJH = TJ + 1;       // face buffers
+// ring records: rows padded to 37 so that the column-wise accesses of the
+// i-halo warp fall on distinct banks
+constexpr int RR = RW + 1, RPL = RR * RH;
+constexpr int NS = 4;                           // ring depth (planes)
+constexpr int GIW = TI + 3, GJH = TJ + 2;       // node buffers: columns -1..TI (padded) / rows -1..TJ
+constexpr int HIW = TI + 3, HJH = TJ + 1;       // face buffers: i faces 0..TI (padded) / j faces 0..TJ
 constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
 constexpr size_t RAW_B = al(4 * 5 * PL);
-constexpr size_t QV_B = al(16 * NQS * PL), QE_B = al(4 * NQS * PL);
-constexpr size_t PV_B = al(16 * NPS * PL), PP_B = al(4 * NPS * PL);
+constexpr size_t QV_B = al(16 * NS * RPL), QE_B = al(4 * NS * RPL);
+constexpr size_t PV_B = al(16 * NS * RPL), PP_B = al(4 * NS * RPL);
 constexpr size_t MET_B = al(4 * 10 * MPL);
+constexpr int UPL = RW * TJ;                     // Q^(0) box: tile rows, 36 columns
+constexpr size_t Q0_B = al(4 * 5 * UPL);
 constexpr size_t GI4_B = al(16 * TJ * GIW), GI1_B = al(4 * TJ * GIW);
 constexpr size_t GJ4_B = al(16 * GJH * TI), GJ1_B = al(4 * GJH * TI);
 constexpr size_t LI_B = al(8 * TJ * GIW), LJ_B = al(8 * GJH * TI);
@@ -66,7 +71,8 @@ constexpr size_t O_QE = O_QV + QV_B;
 constexpr size_t O_PV = O_QE + QE_B;
 constexpr size_t O_PP = O_PV + PV_B;
 constexpr size_t O_MET = O_PP + PP_B;
-constexpr size_t O_GI4 = O_MET + MET_B;
+constexpr size_t O_Q0 = O_MET + MET_B;
+constexpr size_t O_GI4 = O_Q0 + Q0_B;
 constexpr size_t O_GI1 = O_GI4 + GI4_B;
 constexpr size_t O_GJ4 = O_GI1 + GI1_B;
 constexpr size_t O_GJ1 = O_GJ4 + GJ4_B;
@@ -85,8 +91,9 @@ static_assert(O_BAR - O_SCR >= 3 * RAW_B, "prologue staging does not fit");
 static_assert(BYTES <= 232448, "shared memory");
 constexpr uint32_t RAW_TX = 4 * 5 * PL;
 constexpr uint32_t MET_TX = 4 * 10 * MPL;
-// mbarriers: 0 raw buffer, 1..3 prologue staging, 4 metrics
-constexpr int B_RAW = 0, B_MET = 4, NBAR = 5;
+constexpr uint32_t Q0_TX = 4 * 5 * UPL;
+// mbarriers: 0 raw buffer, 1..3 prologue staging, 4 metrics, 5 Q^(0)
+constexpr int B_RAW = 0, B_MET = 4, B_Q0 = 5, NBAR = 6;
 }  // namespace vr
 
 __device__ __forceinline__ void ld5(const float4* v4, const float* v1, int i, float q[5]) {
@@ -113,21 +120,21 @@ __device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity) {
 template <int DIR>
 __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const float* __restrict__ PP,
                                        const float4* __restrict__ QV, const float* __restrict__ QE,
-                                       const float* __restrict__ met, int sM, int sC, int sP, int qC, int x, int y,
+                                       const float* __restrict__ met, int sM, int sC, int sP, int x, int y,
                                        const KConst<float>& c, float G[3][5], float lt[3], float nu[3], float& Jn) {
   using namespace vr;
-  const int o = (y + 2) * RW + x + 2;
+  const int o = (y + 2) * RR + x + 2;
   const int mo = (y + 1) * RW + x + 2;
   float S[9];
 #pragma unroll
   for (int f = 0; f < 9; ++f) S[f] = met[f * MPL + mo];
   Jn = met[9 * MPL + mo];
-  const float4* pc = PV + sC * PL;
+  const float4* pc = PV + sC;
   const float4 r0 = pc[o];
   const float u = r0.x, v = r0.y, w = r0.z, T = r0.w;
-  const float p = PP[sC * PL + o];
-  const float rho = QV[qC * PL + o].x;
-  const float e = QE[qC * PL + o];
+  const float p = PP[sC + o];
+  const float rho = QV[sC + o].x;
+  const float e = QE[sC + o];
   constexpr int K0 = DIR == 0 ? 0 : DIR - 1;
   constexpr int K1 = DIR == 0 ? 3 : DIR;
 
@@ -138,8 +145,8 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
     for (int q = 0; q < 4; ++q) Fv[m][q] = 0.f;
   if (c.viscous) {
     // Cartesian gradients of u, v, w, T: J/2 sum_k S^k_m (phi_+ - phi_-)
-    const float4 a0 = pc[o + 1], b0 = pc[o - 1], a1 = pc[o + RW], b1 = pc[o - RW];
-    const float4 a2 = PV[sP * PL + o], b2 = PV[sM * PL + o];
+    const float4 a0 = pc[o + 1], b0 = pc[o - 1], a1 = pc[o + RR], b1 = pc[o - RR];
+    const float4 a2 = PV[sP + o], b2 = PV[sM + o];
     const float d0[4] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z, a0.w - b0.w};
     const float d1[4] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z, a1.w - b1.w};
     const float d2[4] = {a2.x - b2.x, a2.y - b2.y, a2.z - b2.z, a2.w - b2.w};
@@ -202,9 +209,9 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
       lt[k] = lam[k] * (1.f + Fn<float>::powp(Fn<float>::div(lam[a], lam[k]), c.sigma) +
                         Fn<float>::powp(Fn<float>::div(lam[b], lam[k]), c.sigma));
     float pm, pp;
-    if (k == 0) { pm = PP[sC * PL + o - 1]; pp = PP[sC * PL + o + 1]; }
-    else if (k == 1) { pm = PP[sC * PL + o - RW]; pp = PP[sC * PL + o + RW]; }
-    else { pm = PP[sM * PL + o]; pp = PP[sP * PL + o]; }
+    if (k == 0) { pm = PP[sC + o - 1]; pp = PP[sC + o + 1]; }
+    else if (k == 1) { pm = PP[sC + o - RR]; pp = PP[sC + o + RR]; }
+    else { pm = PP[sM + o]; pp = PP[sP + o]; }
     nu[k] = Fn<float>::div(fabsf(pp - 2.f * p + pm), pp + 2.f * p + pm);
   }
 }
@@ -258,6 +265,13 @@ struct Smem {
     Hj1 = reinterpret_cast<float*>(s + O_HJ1);
     bar = reinterpret_cast<uint64_t*>(s + O_BAR);
   }
+};
+
+// A thread's own node data of one plane, kept in registers from the node
+// pass to the face pass.
+struct Own {
+  float Gi[5], Gj[5];  // node fluxes G^i, G^j
+  float2 Li, Lj;       // (lambda~, nu) in i and j
 };
 
 // One work item: tile (bx, by), k-chunk bz of grid X, stage st.  The CTA's
@@ -336,117 +350,148 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     }
     ok = ok && r;
   };
-  auto qslot = [&](int p) { return (p - pbase) % NQS; };
-  auto pslot = [&](int p) { return (p - pbase) & (NPS - 1); };
+  // ring slot of plane p (both rings): (p - pbase) mod 4
+  auto slot = [&](int p) { return ((p - pbase) & (NS - 1)) * RPL; };
 
   // convert staged plane p (planar, in src) into the ring records
   auto convert = [&](const float* src, int p) {
-    float4* qv = sm.QV + qslot(p) * PL;
-    float* qe = sm.QE + qslot(p) * PL;
-    float4* pv = sm.PV + pslot(p) * PL;
-    float* pp = sm.PP + pslot(p) * PL;
+    const int s = slot(p);
+    float4* qv = sm.QV + s;
+    float* qe = sm.QE + s;
+    float4* pv = sm.PV + s;
+    float* pp = sm.PP + s;
     // halo threads (lighter elsewhere) take the second round first
     for (int e = (tid + NJH + NIH) % NT; e < PL; e += NT) {
       const float q0 = src[e], q1 = src[PL + e], q2 = src[2 * PL + e], q3 = src[3 * PL + e], q4 = src[4 * PL + e];
       const float ri = Fn<float>::rcp(q0);
       const float u = q1 * ri, v = q2 * ri, w = q3 * ri;
       const float pr = c.gm1 * (q4 - 0.5f * q0 * (u * u + v * v + w * w));
-      qv[e] = make_float4(q0, q1, q2, q3);
-      qe[e] = q4;
-      pv[e] = make_float4(u, v, w, c.gamma * pr * ri);
-      pp[e] = pr;
+      const int r = e + e / RW;  // padded ring row
+      qv[r] = make_float4(q0, q1, q2, q3);
+      qe[r] = q4;
+      pv[r] = make_float4(u, v, w, c.gamma * pr * ri);
+      pp[r] = pr;
     }
   };
 
-  // node pass for plane kk: i/j node data to shared memory, k data returned
-  auto node_pass = [&](int kk, float G3[5], float& lt3, float& nu3, float& Jn) {
-    const int sM = pslot(kk - 1), sC = pslot(kk), sP = pslot(kk + 1), qC = qslot(kk);
+  // node pass for plane kk: i/j node data to shared memory (for the
+  // neighbours' faces) and in registers (for this thread's own faces), k data
+  // in registers
+  auto node_pass = [&](int kk, Own& w, float G3[5], float& lt3, float& nu3, float& Jn) {
+    const int sM = slot(kk - 1), sC = slot(kk), sP = slot(kk + 1);
     float G[3][5], lt[3], nu[3];
     if (role == 0) {
-      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jn);
-      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, G[0]);
-      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, G[1]);
-      sm.Li[ny * GIW + nx + 1] = make_float2(lt[0], nu[0]);
-      sm.Lj[(ny + 1) * TI + nx] = make_float2(lt[1], nu[1]);
+      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jn);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) G3[v] = G[2][v];
+      for (int v = 0; v < 5; ++v) {
+        w.Gi[v] = G[0][v];
+        w.Gj[v] = G[1][v];
+        G3[v] = G[2][v];
+      }
+      w.Li = make_float2(lt[0], nu[0]);
+      w.Lj = make_float2(lt[1], nu[1]);
+      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, w.Gi);
+      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, w.Gj);
+      sm.Li[ny * GIW + nx + 1] = w.Li;
+      sm.Lj[(ny + 1) * TI + nx] = w.Lj;
       lt3 = lt[2];
       nu3 = nu[2];
     } else if (role == 1) {
       float Jh;
-      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
-      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, G[0]);
-      sm.Li[ny * GIW + nx + 1] = make_float2(lt[0], nu[0]);
+      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { w.Gi[v] = G[0][v]; w.Gj[v] = 0.f; }
+      w.Li = make_float2(lt[0], nu[0]);
+      w.Lj = make_float2(0.f, 0.f);
+      st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, w.Gi);
+      sm.Li[ny * GIW + nx + 1] = w.Li;
     } else {
       float Jh;
-      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
-      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, G[1]);
-      sm.Lj[(ny + 1) * TI + nx] = make_float2(lt[1], nu[1]);
+      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { w.Gj[v] = G[1][v]; w.Gi[v] = 0.f; }
+      w.Lj = make_float2(lt[1], nu[1]);
+      w.Li = make_float2(0.f, 0.f);
+      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, w.Gj);
+      sm.Lj[(ny + 1) * TI + nx] = w.Lj;
     }
   };
 
-  // i/j face fluxes of plane kk
-  auto face_pass = [&](int kk) {
-    const float4* qv = sm.QV + qslot(kk) * PL;
-    const float* qe = sm.QE + qslot(kk) * PL;
-    auto iface = [&](int x, int y) {  // face between x-1 and x in row y
-      float Ga[5], Gb[5], q[4][5], h[5];
-      ld5(sm.Gi4, sm.Gi1, y * GIW + x, Ga);
-      ld5(sm.Gi4, sm.Gi1, y * GIW + x + 1, Gb);
-      const int base = (y + 2) * RW + x;  // node x-2
-#pragma unroll
-      for (int n = 0; n < 4; ++n) ld5(qv, qe, base + n, q[n]);
-      face_v(c, sm.Li[y * GIW + x], sm.Li[y * GIW + x + 1], Ga, Gb, q[0], q[1], q[2], q[3], h);
-      st5(sm.Hi4, sm.Hi1, y * HIW + x, h);
-    };
-    auto jface = [&](int x, int y) {  // face between y-1 and y in column x
-      float Ga[5], Gb[5], q[4][5], h[5];
-      ld5(sm.Gj4, sm.Gj1, y * TI + x, Ga);
-      ld5(sm.Gj4, sm.Gj1, (y + 1) * TI + x, Gb);
-      const int base = y * RW + x + 2;  // node y-2
-#pragma unroll
-      for (int n = 0; n < 4; ++n) ld5(qv, qe, base + n * RW, q[n]);
-      face_v(c, sm.Lj[y * TI + x], sm.Lj[(y + 1) * TI + x], Ga, Gb, q[0], q[1], q[2], q[3], h);
-      st5(sm.Hj4, sm.Hj1, y * TI + x, h);
-    };
-    if (role == 0) {
-      iface(nx, ny);
-      jface(nx, ny);
-    } else {
-      const int h = tid - NTILE;  // the last i-face of each row and j-face of each column
-      if (h < TJ) iface(TI, h);
-      else if (h < TJ + TI) jface(h - TJ, TJ);
+  // face fluxes of plane kk on the low side of this thread's node: i face
+  // between nx-1 and nx (tile nodes and the i-halo column TI), j face between
+  // ny-1 and ny (tile nodes and the j-halo row TJ).  The node's own G, (lt, nu)
+  // and conserved record come from registers; qo returns the record.
+  const bool do_i = role == 0 || (role == 1 && nx == TI);
+  const bool do_j = role == 0 || (role == 2 && ny == TJ);
+  const int oo = (ny + 2) * RR + nx + 2;  // this thread's node in a ring plane
+  auto face_pass = [&](int kk, const Own& w, float hi[5], float hj[5], float qo[5]) {
+    const float4* qv = sm.QV + slot(kk);
+    const float* qe = sm.QE + slot(kk);
+    if (do_i || do_j) ld5(qv, qe, oo, qo);
+    if (do_i) {
+      float Ga[5], q0[5], q1[5], q3[5];
+      ld5(sm.Gi4, sm.Gi1, ny * GIW + nx, Ga);
+      ld5(qv, qe, oo - 2, q0);
+      ld5(qv, qe, oo - 1, q1);
+      ld5(qv, qe, oo + 1, q3);
+      face_v(c, sm.Li[ny * GIW + nx], w.Li, Ga, w.Gi, q0, q1, qo, q3, hi);
+      st5(sm.Hi4, sm.Hi1, ny * HIW + nx, hi);
+    }
+    if (do_j) {
+      float Ga[5], q0[5], q1[5], q3[5];
+      ld5(sm.Gj4, sm.Gj1, ny * TI + nx, Ga);
+      ld5(qv, qe, oo - 2 * RR, q0);
+      ld5(qv, qe, oo - RR, q1);
+      ld5(qv, qe, oo + RR, q3);
+      face_v(c, sm.Lj[ny * TI + nx], w.Lj, Ga, w.Gj, q0, q1, qo, q3, hj);
+      st5(sm.Hj4, sm.Hj1, ny * TI + nx, hj);
     }
   };
 
-  // i/j residual of this thread's tile node
-  auto rij = [&](float R[5]) {
-    float a[5], b[5], cc[5], d[5];
+  // i/j residual of this thread's tile node: the high-side faces come from
+  // the neighbours, the low-side j face from registers (keeping the low-side
+  // i face as well would exceed the register budget)
+  auto rij = [&](const float hj[5], float R[5]) {
+    float a[5], b[5], d[5];
     ld5(sm.Hi4, sm.Hi1, ny * HIW + nx + 1, a);
-    ld5(sm.Hi4, sm.Hi1, ny * HIW + nx, b);
-    ld5(sm.Hj4, sm.Hj1, (ny + 1) * TI + nx, cc);
-    ld5(sm.Hj4, sm.Hj1, ny * TI + nx, d);
+    ld5(sm.Hi4, sm.Hi1, ny * HIW + nx, d);
+    ld5(sm.Hj4, sm.Hj1, (ny + 1) * TI + nx, b);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) R[v] = (a[v] - b[v]) + (cc[v] - d[v]);
+    for (int v = 0; v < 5; ++v) R[v] = (a[v] - d[v]) + (b[v] - hj[v]);
   };
 
-  // k face flux between planes ka and ka+1 of this thread's column
+  // k face flux between planes ka and ka+1 of this thread's column; q1 is
+  // the conserved record of plane ka+1 (already in registers)
   auto kface = [&](int ka, const float Ga[5], const float Gb[5], float lta, float ltb, float nua, float nub,
-                   float h[5]) {
-    const int o = (ny + 2) * RW + nx + 2;
-    float q[4][5];
-#pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      const int s = qslot(ka - 1 + n);
-      ld5(sm.QV + s * PL, sm.QE + s * PL, o, q[n]);
-    }
-    face_v(c, make_float2(lta, nua), make_float2(ltb, nub), Ga, Gb, q[0], q[1], q[2], q[3], h);
+                   const float q1[5], float h[5]) {
+    float qm[5], qa[5], qp[5];
+    int s = slot(ka - 1);
+    ld5(sm.QV + s, sm.QE + s, oo, qm);
+    s = slot(ka);
+    ld5(sm.QV + s, sm.QE + s, oo, qa);
+    s = slot(ka + 2);
+    ld5(sm.QV + s, sm.QE + s, oo, qp);
+    face_v(c, make_float2(lta, nua), make_float2(ltb, nub), Ga, Gb, qm, qa, q1, qp, h);
   };
 
   const float adt = (float)(st.alpha * X.sc->dt);
   const long long npad = L.npad;
   float* const Qo = X.Q[st.qout];
-  const float* const Q0 = X.Q[0];
+  // Q^(0) of the plane being updated: for the first stage it is the stage
+  // input, still in the conserved ring; otherwise TMA stages it one plane
+  // ahead (tile rows, 36 columns from the aligned column i0-2)
+  const bool q0_ring = st.qin == 0;
+  const float* q0buf = reinterpret_cast<const float*>(smem + O_Q0);
+  auto issue_q0 = [&](int p) {
+    if (tid == 0 && !q0_ring) {
+      pend |= 1u << B_Q0;
+      ppar = (ppar & ~(1u << B_Q0)) | ((uint32_t)((p - t0) & 1) << B_Q0);
+      fence_async_shared();
+      mbar_expect_tx(&sm.bar[B_Q0], Q0_TX);
+      tma_load_4d(smem + O_Q0, &X.tmQ0u, &sm.bar[B_Q0], i0, j0 + 2, p + NG, 0);
+    }
+  };
+  long long n_t0 = own ? L.at(gi, gj, t0) : 0;  // this thread's node in plane t0
   float* scr[3] = {reinterpret_cast<float*>(smem + O_SCR), reinterpret_cast<float*>(smem + O_SCR + RAW_B),
                    reinterpret_cast<float*>(smem + O_SCR + 2 * RAW_B)};
 
@@ -471,46 +516,54 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     float G3m[5], lt3m = 0.f, nu3m = 0.f, Jm = 0.f;
     float G3c[5], lt3c = 0.f, nu3c = 0.f, Jc = 0.f;
     float Rc[5], hprev[5];
+    Own w;
     wait(B_MET, met_parity(t0 - 1), t0 - 1);
-    node_pass(t0 - 1, G3m, lt3m, nu3m, Jm);
+    node_pass(t0 - 1, w, G3m, lt3m, nu3m, Jm);
     if (__syncthreads_or(!ok)) goto fail;
     issue_met(t0);
     wait(B_MET, met_parity(t0), t0);
-    node_pass(t0, G3c, lt3c, nu3c, Jc);
+    node_pass(t0, w, G3c, lt3c, nu3c, Jc);
     if (__syncthreads_or(!ok)) goto fail;
     issue_met(t0 + 1);
-    face_pass(t0);
-    __syncthreads();
-    if (role == 0) {
-      rij(Rc);
-      kface(t0 - 1, G3m, G3c, lt3m, lt3c, nu3m, nu3c, hprev);
+    {
+      float hi[5], hj[5], qo[5];
+      face_pass(t0, w, hi, hj, qo);
+      if (role == 0) kface(t0 - 1, G3m, G3c, lt3m, lt3c, nu3m, nu3c, qo, hprev);
+      __syncthreads();
+      if (role == 0) rij(hj, Rc);
     }
+    // ring slot of plane t0-2 is free: its last readers were the k face above
     wait(B_RAW, raw_parity(t0 + 2), t0 + 2);
     convert(sm.raw, t0 + 2);
     if (__syncthreads_or(!ok)) goto fail;
     if (t0 + 3 <= t1 + 1) issue_raw(t0 + 3, B_RAW, sm.raw, raw_parity(t0 + 3));
+    issue_q0(t0);
 
     // ---- march in k: iteration t writes plane t
     for (int t = t0; t < t1; ++t) {
       float G3n[5], lt3n = 0.f, nu3n = 0.f, Jn = 0.f;
       wait(B_MET, met_parity(t + 1), t + 1);
-      node_pass(t + 1, G3n, lt3n, nu3n, Jn);
+      node_pass(t + 1, w, G3n, lt3n, nu3n, Jn);
       if (__syncthreads_or(!ok)) goto fail;
       if (t + 2 <= t1) issue_met(t + 2);
-      float q0[5];
-      long long n = 0;
-      if (own) {
-        n = L.at(gi, gj, t);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) q0[v] = Q0[v * npad + n];
-      }
-      face_pass(t + 1);
+      float hi[5], hj[5], qo[5], hk[5];
+      face_pass(t + 1, w, hi, hj, qo);
+      if (role == 0) kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, qo, hk);
       __syncthreads();
+      if (!q0_ring) wait(B_Q0, (uint32_t)((t - t0) & 1), t);
       if (role == 0) {
-        float Rn[5], hk[5];
-        rij(Rn);
-        kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, hk);
+        float Rn[5];
+        rij(hj, Rn);
         if (own) {
+          float q0[5];
+          if (q0_ring) {
+            const int s = slot(t);
+            ld5(sm.QV + s, sm.QE + s, oo, q0);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) q0[v] = q0buf[v * UPL + ny * RW + nx + 2];
+          }
+          const long long n = n_t0 + (long long)(t - t0) * L.plane;
 #pragma unroll
           for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
         }
@@ -524,12 +577,14 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
         nu3c = nu3n;
         Jc = Jn;
       }
+      // plane t+3 takes the ring slot of plane t-1 (last read by the k face)
       if (t + 3 <= t1 + 1) {
         wait(B_RAW, raw_parity(t + 3), t + 3);
         convert(sm.raw, t + 3);
       }
       if (__syncthreads_or(!ok)) goto fail;
       if (t + 4 <= t1 + 1) issue_raw(t + 4, B_RAW, sm.raw, raw_parity(t + 4));
+      if (t + 1 < t1) issue_q0(t + 1);
     }
   }
   return true;
