@@ -148,7 +148,7 @@ struct jz_batch {
   int prec = 0;
   char* dev = nullptr;
   size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0;
-  int nitems = 0, bc_nodes_blocks = 1, bc_ghost_blocks = 1;
+  int nitems = 0, bc_blocks = 1;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   double graph_cfl = -1.0;
@@ -633,7 +633,7 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
     e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
                            (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
-    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_nodes_blocks, b->bc_ghost_blocks, out[l], s);
+    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched boundary launch failed: %s", cudaGetErrorString(e));
   }
   return JZ_OK;
@@ -660,13 +660,12 @@ int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, v
   if (bytes < P.total) return fail(JZ_ENOMEM, "batch buffer holds %zu bytes, batch needs %zu", bytes, P.total);
   const int prec = grids[0]->dev.prec;
   std::vector<char> host(P.total, 0);
-  int nb = 1, gb = 1;
+  int nb = 1;
   for (int k = 0; k < n; ++k) {
     stage_ctx_fill(host.data() + P.off_stage + (size_t)k * stage_ctx_bytes(prec), grids[k]->dev);
-    int a = 1, c = 1;
-    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a, &c);
+    int a = 1;
+    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a);
     nb = std::max(nb, a);
-    gb = std::max(gb, c);
     rate_ctx_fill(host.data() + P.off_rate + (size_t)k * rate_ctx_bytes(), grids[k]->dev);
   }
   memcpy(host.data() + P.off_items, P.items.data(), P.items.size() * sizeof(int4));
@@ -683,8 +682,7 @@ int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, v
   b->off_items = P.off_items;
   b->off_queue = P.off_queue;
   b->nitems = (int)P.items.size();
-  b->bc_nodes_blocks = nb;
-  b->bc_ghost_blocks = gb;
+  b->bc_blocks = nb;
   *out = b;
   return JZ_OK;
 }

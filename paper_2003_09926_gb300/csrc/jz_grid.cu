@@ -286,53 +286,44 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
   return true;
 }
 
-// Boundary fill, pass 1: every boundary node (a grid node outside the
-// updated box) takes its boundary-condition value.  Only interior nodes are
-// read, so the pass is race-free.
+// Boundary fill in one pass over the padded nodes outside the updated box:
+// each takes the value of the grid node its index maps to (wrap, or clamp
+// onto the two ghost layers): a copy when that node is updated by the
+// stages, its boundary-condition value (computed here from the interior
+// node it reads) when it is a boundary node.  Only updated nodes are read,
+// so the pass is race-free in one launch, and every node gets the value of
+// a boundary pass followed by a ghost copy.
 template <typename ST, typename MT>
-__device__ __forceinline__ void bc_nodes_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
-                                              const FlowC& F, ST* __restrict__ Q, const MT* __restrict__ M) {
-  const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-    int i, j, k;
-    slab_node(sl, q, t, i, j, k);
-    ST v[5];
-    boundary_value<ST, MT>(L, inflow, F, Q, M, i, j, k, v);
-    const long long g = L.at(i, j, k);
-    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = v[c];
-  }
-}
-
-// Boundary fill, pass 2: every ghost node copies the grid node its index
-// maps to (clamp, or wrap in periodic directions).
-template <typename ST>
-__device__ __forceinline__ void ghosts_slab(const Layout& L, const Slabs& sl, int q, ST* __restrict__ Q) {
+__device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
+                                          const FlowC& F, ST* __restrict__ Q, const MT* __restrict__ M) {
   const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
     int i, j, k;
     slab_node(sl, q, t, i, j, k);
     const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
     const int mk = map_index(k, L.n[2], L.per[2]);
-    const long long g = L.at(i, j, k), src = L.at(mi, mj, mk);
-    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = Q[(long long)c * L.npad + src];
+    ST v[5];
+    if (mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2]) {
+      const long long src = L.at(mi, mj, mk);
+      for (int c = 0; c < 5; ++c) v[c] = Q[(long long)c * L.npad + src];
+    } else {
+      boundary_value<ST, MT>(L, inflow, F, Q, M, mi, mj, mk, v);
+    }
+    const long long g = L.at(i, j, k);
+    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = v[c];
   }
 }
 
 template <typename ST, typename MT>
-__global__ void k_bc_nodes(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
-                           const MT* __restrict__ M) {
-  bc_nodes_slab<ST, MT>(L, sl, blockIdx.y, inflow, F, Q, M);
-}
-
-template <typename ST>
-__global__ void k_ghosts(Layout L, Slabs sl, ST* __restrict__ Q) {
-  ghosts_slab<ST>(L, sl, blockIdx.y, Q);
+__global__ void k_bc_fill(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
+                          const MT* __restrict__ M) {
+  fill_slab<ST, MT>(L, sl, blockIdx.y, inflow, F, Q, M);
 }
 
 // batched versions: grid blockIdx.z of the table, state copy `which`
 struct BcCtx {
   Layout L;
-  Slabs nodes, ghosts;
+  Slabs fill;
   const double* inflow;
   FlowC F;
   void* Q[3];
@@ -340,15 +331,9 @@ struct BcCtx {
 };
 
 template <typename ST, typename MT>
-__global__ void k_bc_nodes_batch(const BcCtx* __restrict__ ctx, int which) {
+__global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
   const BcCtx& X = ctx[blockIdx.z];
-  bc_nodes_slab<ST, MT>(X.L, X.nodes, blockIdx.y, X.inflow, X.F, (ST*)X.Q[which], (const MT*)X.M);
-}
-
-template <typename ST>
-__global__ void k_ghosts_batch(const BcCtx* __restrict__ ctx, int which) {
-  const BcCtx& X = ctx[blockIdx.z];
-  ghosts_slab<ST>(X.L, X.ghosts, blockIdx.y, (ST*)X.Q[which]);
+  fill_slab<ST, MT>(X.L, X.fill, blockIdx.y, X.inflow, X.F, (ST*)X.Q[which], (const MT*)X.M);
 }
 
 // axial inflow velocity of the jet profile at the x- face nodes (FP64, once per state_init)
@@ -470,13 +455,11 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-void bc_slabs(const Layout& L, Slabs& nodes, Slabs& ghosts) {
+// the padded nodes outside the updated box [lo, hi]
+Slabs bc_slabs(const Layout& L) {
   const int pad_lo[3] = {-NG, -NG, -NG};
   const int pad_hi[3] = {L.n[0] + 1, L.n[1] + 1, L.n[2] + 1};
-  const int grid_lo[3] = {0, 0, 0};
-  const int grid_hi[3] = {L.n[0] - 1, L.n[1] - 1, L.n[2] - 1};
-  nodes = make_slabs(grid_lo, grid_hi, L.lo, L.hi);
-  ghosts = make_slabs(pad_lo, pad_hi, grid_lo, grid_hi);
+  return make_slabs(pad_lo, pad_hi, L.lo, L.hi);
 }
 
 int slab_blocks(const Slabs& sl) {
@@ -490,63 +473,48 @@ int slab_blocks(const Slabs& sl) {
 }
 
 cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
-  Slabs nodes, ghosts;
-  bc_slabs(g.L, nodes, ghosts);
-  const dim3 bn(slab_blocks(nodes), 6), bg(slab_blocks(ghosts), 6);
+  const Slabs sl = bc_slabs(g.L);
+  const dim3 b(slab_blocks(sl), 6);
   switch (g.prec) {
     case JZ_P64:
-      k_bc_nodes<double, double><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (double*)Q, (const double*)g.M);
-      k_ghosts<double><<<bg, 256, 0, s>>>(g.L, ghosts, (double*)Q);
+      k_bc_fill<double, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (double*)Q, (const double*)g.M);
       break;
     case JZ_P32_M64:
-      k_bc_nodes<float, double><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (float*)Q, (const double*)g.M);
-      k_ghosts<float><<<bg, 256, 0, s>>>(g.L, ghosts, (float*)Q);
+      k_bc_fill<float, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (float*)Q, (const double*)g.M);
       break;
     default:
-      k_bc_nodes<float, float><<<bn, 256, 0, s>>>(g.L, nodes, g.inflow, g.F, (float*)Q, (const float*)g.M);
-      k_ghosts<float><<<bg, 256, 0, s>>>(g.L, ghosts, (float*)Q);
+      k_bc_fill<float, float><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (float*)Q, (const float*)g.M);
       break;
   }
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 size_t bc_ctx_bytes() { return sizeof(BcCtx); }
 
-// fills the host-side table entry; returns the block counts both passes need
-void bc_ctx_fill(void* dst, const GridDev& g, int* nodes_blocks, int* ghost_blocks) {
+// fills the host-side table entry; returns the block count the fill needs
+void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
   BcCtx& X = *(BcCtx*)dst;
   X.L = g.L;
-  bc_slabs(g.L, X.nodes, X.ghosts);
+  X.fill = bc_slabs(g.L);
   X.inflow = g.inflow;
   X.F = g.F;
   X.Q[0] = g.Q0;
   X.Q[1] = g.QA;
   X.Q[2] = g.QB;
   X.M = g.M;
-  *nodes_blocks = slab_blocks(X.nodes);
-  *ghost_blocks = slab_blocks(X.ghosts);
+  *blocks = slab_blocks(X.fill);
 }
 
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int nodes_blocks, int ghost_blocks, int which,
-                            cudaStream_t s) {
-  const dim3 bn(nodes_blocks, 6, n), bg(ghost_blocks, 6, n);
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, cudaStream_t s) {
+  const dim3 b(blocks, 6, n);
   const BcCtx* X = (const BcCtx*)ctx;
   switch (prec) {
-    case JZ_P64:
-      k_bc_nodes_batch<double, double><<<bn, 256, 0, s>>>(X, which);
-      k_ghosts_batch<double><<<bg, 256, 0, s>>>(X, which);
-      break;
-    case JZ_P32_M64:
-      k_bc_nodes_batch<float, double><<<bn, 256, 0, s>>>(X, which);
-      k_ghosts_batch<float><<<bg, 256, 0, s>>>(X, which);
-      break;
-    default:
-      k_bc_nodes_batch<float, float><<<bn, 256, 0, s>>>(X, which);
-      k_ghosts_batch<float><<<bg, 256, 0, s>>>(X, which);
-      break;
+    case JZ_P64: k_bc_fill_batch<double, double><<<b, 256, 0, s>>>(X, which); break;
+    case JZ_P32_M64: k_bc_fill_batch<float, double><<<b, 256, 0, s>>>(X, which); break;
+    default: k_bc_fill_batch<float, float><<<b, 256, 0, s>>>(X, which); break;
   }
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -60,9 +60,8 @@ cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
 
 // batched boundary fill over a device table of per-grid contexts
 size_t bc_ctx_bytes();
-void bc_ctx_fill(void* host_dst, const GridDev& g, int* nodes_blocks, int* ghost_blocks);
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int nodes_blocks, int ghost_blocks, int which,
-                            cudaStream_t s);
+void bc_ctx_fill(void* host_dst, const GridDev& g, int* blocks);
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, cudaStream_t s);
 
 // jz_reduce.cu
 cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s);

@@ -47,33 +47,53 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
   const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
   const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
   const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
-  double best = 0.0;
-  // warp w of the fixed grid visits rows r = w, w + W, ... (r = j + nj k); lanes walk i
+  // the maximum is taken in the arithmetic type: exact, and the same value
+  // as a maximum of the widened rates
+  ST best_s = ST(0);
+  // warp w of the fixed grid visits rows r = w, w + W, ... (r = j + nj k);
+  // lanes walk i, four nodes per lane at a time with all their loads issued
+  // before any arithmetic (the kernel is bound by memory latency)
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const int W = (gridDim.x * blockDim.x) >> 5;
   const int rows = L.n[1] * L.n[2];
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += W) {
     const long long row = L.at(0, r % L.n[1], r / L.n[1]);
-    for (int i = lane; i < L.n[0]; i += 32) {
-    const long long n = row + i;
-    ST rho = Q[n], ri = ST(1) / rho;
-    ST u = Q[L.npad + n] * ri, v = Q[2 * L.npad + n] * ri, w = Q[3 * L.npad + n] * ri;
-    ST p = gm1 * (Q[4 * L.npad + n] - ST(0.5) * rho * (u * u + v * v + w * w));
-    ST T = g * p * ri;
-    ST c = sqrt(T);
-    ST nu = vfac * sutherland<ST>(mu_inf, s1, T) * ri;
-    ST Jn = (ST)M[9 * L.npad + n];
-    ST conv = 0, s2 = 0;
-    for (int kd = 0; kd < 3; ++kd) {
-      ST a = (ST)M[(3 * kd) * L.npad + n], b = (ST)M[(3 * kd + 1) * L.npad + n], cc = (ST)M[(3 * kd + 2) * L.npad + n];
-      ST sq = a * a + b * b + cc * cc;
-      conv += Jn * (fabs(a * u + b * v + cc * w) + c * sqrt(sq));
-      s2 += sq;
-    }
-    double rate = (double)(conv + ST(2) * nu * Jn * Jn * s2);
-    best = fmax(best, rate);
+    for (int ib = 0; ib < L.n[0]; ib += 32 * U) {
+      ST q[U][5], m[U][10];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = ib + lane + 32 * u;
+        const long long n = row + (i < L.n[0] ? i : 0);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q[u][v] = Q[v * L.npad + n];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) m[u][f] = (ST)M[f * L.npad + n];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ib + lane + 32 * u >= L.n[0]) continue;
+        const ST rho = q[u][0], ri = ST(1) / rho;
+        const ST uu = q[u][1] * ri, vv = q[u][2] * ri, ww = q[u][3] * ri;
+        const ST p = gm1 * (q[u][4] - ST(0.5) * rho * (uu * uu + vv * vv + ww * ww));
+        const ST T = g * p * ri;
+        const ST c = sqrt(T);
+        const ST nu = vfac * sutherland<ST>(mu_inf, s1, T) * ri;
+        const ST Jn = m[u][9];
+        ST conv = 0, s2 = 0;
+#pragma unroll
+        for (int kd = 0; kd < 3; ++kd) {
+          const ST a = m[u][3 * kd], b = m[u][3 * kd + 1], cc = m[u][3 * kd + 2];
+          const ST sq = a * a + b * b + cc * cc;
+          conv += Jn * (fabs(a * uu + b * vv + cc * ww) + c * sqrt(sq));
+          s2 += sq;
+        }
+        const ST rate = conv + ST(2) * nu * Jn * Jn * s2;
+        best_s = rate > best_s ? rate : best_s;
+      }
     }
   }
+  double best = (double)best_s;
   __shared__ double red[RED_THREADS / 32];
   best = warp_max(best);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;

@@ -234,7 +234,7 @@ def test_launch_counter_advances(jz):
     before = jz.jz_launch_count()
     g.nsteps(3, cfl=0.5)
     g.synchronize()
-    assert jz.jz_launch_count() - before == 3 * 16  # time step, 5 x (stage + boundary nodes + ghosts)
+    assert jz.jz_launch_count() - before == 3 * 11  # time step, 5 x (stage + boundary fill)
 
 
 @pytest.mark.parametrize("variant", [1, 2])
