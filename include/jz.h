@@ -91,8 +91,12 @@ typedef struct jz_flow_params {
   int ic; /* JZ_IC_JET or JZ_IC_QUIESCENT */
 } jz_flow_params;
 
-/* Diagnostics over all grid nodes (ghosts excluded), in FP64, summed in a
- * fixed order (bitwise reproducible run to run). */
+/* Diagnostics over all grid nodes (ghosts excluded), reduced in a fixed
+ * order (bitwise reproducible run to run).  Per-node values are computed in
+ * the state's precision (FP32 for JZ_P32 and JZ_P32_M64 grids); the sums are
+ * carried in FP64 (FP32 grids: compensated FP32 per thread, then FP64), so
+ * an FP32 grid's sums are exact up to the FP32 rounding of 1/J and of the
+ * per-node products Q_v * (1/J): within 2^-23 of sum |Q_v|/J. */
 typedef struct jz_diag {
   double time;      /* simulated time                                  */
   int64_t step;     /* completed time steps                            */
@@ -222,9 +226,11 @@ int jz_set_stage_variant(jz_grid* g, int variant);
  * Q:    device, dense [5][n_nodes] conserved variables (rho, rho u, rho v,
  *       rho w, e), FP64 when fp64 = 1, FP32 when fp64 = 0;
  * vol:  device, n_nodes FP64 node volumes (1/J for a grid);
- * out:  device, 11 doubles: sum Q_v * vol (5), rho min, rho max, p min,
- *       p max, max |u|/c, count of nodes with a non-finite value (nodes
- *       with one are left out of the sums and extrema);
+ * out:  device, 11 doubles: sum Q_v * vol (5, in FP64), rho min, rho max,
+ *       p min, p max, max |u|/c (pressure and Mach number computed per node
+ *       in the state's precision, as jz_diagnostics does), count of nodes
+ *       with a non-finite value (nodes with one are left out of the sums and
+ *       extrema);
  * stream: cudaStream_t as void* (NULL = legacy default stream).
  * n_nodes must not exceed 268,435,456 (2^28; JZ_EINVAL beyond).  The work is
  * enqueued asynchronously; results are summed in a fixed order (bitwise

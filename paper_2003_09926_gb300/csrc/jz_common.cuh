@@ -103,6 +103,36 @@ __host__ __device__ __forceinline__ double unit53(uint64_t r) {
 
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Per-node diagnostic quantities of a conserved state q, in the state's
+// arithmetic type T: pressure and the squared Mach number (the maximum over
+// nodes is taken on the square; its root is taken once at the end).
+template <typename T>
+__host__ __device__ __forceinline__ void diag_node(const T q[5], T gm1, T gamma, T& p, T& m2) {
+  const T ri = T(1) / q[0];
+  const T k = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) * ri;  // rho |u|^2
+  p = gm1 * (q[4] - T(0.5) * k);
+  m2 = k / (gamma * p);  // |u|^2 / c^2 with c^2 = gamma p / rho
+}
+
+// Running sum of one conserved variable: plain FP64 for FP64 states; for
+// FP32 states an FP32 sum with the rounding error of every addition carried
+// in a second FP32 word (Knuth's TwoSum), folded to FP64 at the end.
+template <typename T> struct RunSum;
+template <> struct RunSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct RunSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x, bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // launch accounting (defined in jz_api.cu)
 void count_launches(uint64_t n);
 

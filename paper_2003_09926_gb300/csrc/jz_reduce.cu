@@ -152,38 +152,56 @@ __global__ void k_fixed_dt(Scalars* sc, double dt) {
 }
 
 // Diagnostics partial per thread / block:
-//   [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min, [8] p max, [9] mach max, [10] non-finite count
+//   [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min, [8] p max,
+//   [9] max of the squared Mach number, [10] non-finite count.
+// Per-node arithmetic in the state's type; each lane takes four nodes of its
+// row at a time with all their loads issued first.
 template <typename ST, typename MT>
 __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const ST* __restrict__ Q,
                                                       const MT* __restrict__ M, Scalars* sc, double* partial) {
-  const double gm1 = F.gm1, g = F.gamma;
-  double acc[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
-  // fixed visiting order: warp w takes rows w, w + W, ...; lanes walk i
+  const ST gm1 = (ST)F.gm1, g = (ST)F.gamma;
+  RunSum<ST> sum[5];
+  ST rmin = ST(INFINITY), rmax = ST(-INFINITY), pmin = ST(INFINITY), pmax = ST(-INFINITY), m2max = ST(0);
+  double nonfinite = 0.0;
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const int W = (gridDim.x * blockDim.x) >> 5;
   const int rows = L.n[1] * L.n[2];
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += W) {
     const long long row = L.at(0, r % L.n[1], r / L.n[1]);
-    for (int i = lane; i < L.n[0]; i += 32) {
-    const long long n = row + i;
-    double q[5];
-    bool finite = true;
-    for (int v = 0; v < 5; ++v) {
-      q[v] = (double)Q[(long long)v * L.npad + n];
-      finite = finite && isfinite(q[v]);
-    }
-    if (!finite) { acc[10] += 1.0; continue; }
-    double Jn = (double)M[9 * L.npad + n];
-    for (int v = 0; v < 5; ++v) acc[v] += q[v] / Jn;
-    double rho = q[0], u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
-    double p = gm1 * (q[4] - 0.5 * rho * (u * u + v * v + w * w));
-    acc[5] = fmin(acc[5], rho);
-    acc[6] = fmax(acc[6], rho);
-    acc[7] = fmin(acc[7], p);
-    acc[8] = fmax(acc[8], p);
-    acc[9] = fmax(acc[9], sqrt(u * u + v * v + w * w) / sqrt(g * p / rho));
+    for (int ib = 0; ib < L.n[0]; ib += 32 * U) {
+      ST q[U][5], Jn[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = ib + lane + 32 * u;
+        const long long n = row + (i < L.n[0] ? i : 0);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q[u][v] = Q[(long long)v * L.npad + n];
+        Jn[u] = (ST)M[9 * L.npad + n];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ib + lane + 32 * u >= L.n[0]) continue;
+        bool finite = true;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) finite = finite && isfinite(q[u][v]);
+        if (!finite) { nonfinite += 1.0; continue; }
+        const ST vol = ST(1) / Jn[u];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum[v].add(q[u][v] * vol);
+        ST p, m2;
+        diag_node<ST>(q[u], gm1, g, p, m2);
+        const ST rho = q[u][0];
+        rmin = rho < rmin ? rho : rmin;
+        rmax = rho > rmax ? rho : rmax;
+        pmin = p < pmin ? p : pmin;
+        pmax = p > pmax ? p : pmax;
+        m2max = m2 > m2max ? m2 : m2max;
+      }
     }
   }
+  double acc[DIAG_WORDS] = {sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value(), sum[4].value(),
+                            (double)rmin, (double)rmax, (double)pmin, (double)pmax, (double)m2max, nonfinite};
   __shared__ double sh[DIAG_WORDS][RED_THREADS];
   for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
   __syncthreads();
@@ -235,6 +253,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
     }
     if (threadIdx.x == 0) {
       for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
+      sc->diag[9] = sqrt(sh[9][0]);  // maximum Mach number
       sc->dcount = 0;
     }
   }

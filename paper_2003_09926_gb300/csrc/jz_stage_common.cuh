@@ -89,6 +89,29 @@ template <> struct Fn<double> {
   }
 };
 
+// Packed FP32 pair: two independent lanes of arithmetic in one FP32x2
+// instruction (fadd/fmul/fma .f32x2).
+struct f2 {
+  float2 v;
+  f2() = default;
+  __device__ __forceinline__ f2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ f2(float2 a) : v(a) {}
+};
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+// a - b as one packed FMA: b * (-1) + a
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ f2 abs2(f2 a) { return f2(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return f2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return f2(Fn<float>::sqrt_(a.v.x), Fn<float>::sqrt_(a.v.y)); }
+__device__ __forceinline__ f2 rcp2(f2 a) { return f2(Fn<float>::rcp(a.v.x), Fn<float>::rcp(a.v.y)); }
+__device__ __forceinline__ f2 jm23_2(f2 a) { return f2(Fn<float>::jm23(a.v.x), Fn<float>::jm23(a.v.y)); }
+__device__ __forceinline__ f2 pow2(f2 a, float e) { return f2(Fn<float>::powp(a.v.x, e), Fn<float>::powp(a.v.y, e)); }
+
+
 // ---------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX, sm_90+ async proxy)
 // ---------------------------------------------------------------------------

@@ -226,6 +226,8 @@ __device__ __forceinline__ void face_v(const KConst<float>& c, float2 La, float2
   const float e2 = c.k2 * fmaxf(La.y, Lb.y);
   const float e4 = fmaxf(0.f, c.k4 - e2);
   const float l2 = lam * e2, l4 = lam * e4;
+  // (packed FP32x2 pairs for components 0-3 cut 45 instructions per point
+  // here but measured 1% slower: the kernel is not bound by issue alone)
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const float d1 = qb[v] - qa[v];

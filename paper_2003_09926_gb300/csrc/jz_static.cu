@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(SD_THREADS) k_diag_static(long long n, const S
                                                             double* scratch, double* out) {
   double* partial = scratch;
   unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + SD_MAX_CHUNKS * SD_WORDS);
-  const double gm1 = gamma - 1.0;
+  const ST gm1s = (ST)(gamma - 1.0), gs = (ST)gamma;
   double acc[SD_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
   const long long lo = (long long)blockIdx.x * SD_CHUNK;
   const long long hi = lo + SD_CHUNK < n ? lo + SD_CHUNK : n;
@@ -56,13 +56,16 @@ __global__ void __launch_bounds__(SD_THREADS) k_diag_static(long long n, const S
     if (!finite) { acc[10] += 1.0; continue; }
     const double V = vol[t];
     for (int v = 0; v < 5; ++v) acc[v] += q[v] * V;
-    const double rho = q[0], u = q[1] / rho, v = q[2] / rho, w = q[3] / rho;
-    const double p = gm1 * (q[4] - 0.5 * rho * (u * u + v * v + w * w));
-    acc[5] = fmin(acc[5], rho);
-    acc[6] = fmax(acc[6], rho);
-    acc[7] = fmin(acc[7], p);
-    acc[8] = fmax(acc[8], p);
-    acc[9] = fmax(acc[9], sqrt(u * u + v * v + w * w) / sqrt(gamma * p / rho));
+    // pressure and squared Mach number in the state's type, as the grid
+    // diagnostics compute them
+    ST qs[5], p, m2;
+    for (int v = 0; v < 5; ++v) qs[v] = Q[(long long)v * n + t];
+    diag_node<ST>(qs, gm1s, gs, p, m2);
+    acc[5] = fmin(acc[5], q[0]);
+    acc[6] = fmax(acc[6], q[0]);
+    acc[7] = fmin(acc[7], (double)p);
+    acc[8] = fmax(acc[8], (double)p);
+    acc[9] = fmax(acc[9], (double)m2);
   }
   __shared__ double sh[SD_WORDS][SD_THREADS];
   for (int c = 0; c < SD_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
@@ -102,6 +105,7 @@ __global__ void __launch_bounds__(SD_THREADS) k_diag_static(long long n, const S
       r[10] += x[10];
     }
     for (int c = 0; c < SD_WORDS; ++c) out[c] = r[c];
+    out[9] = sqrt(r[9]);  // maximum Mach number
     *counter = 0;
   }
 }

@@ -27,7 +27,11 @@ def jz():
     return J
 
 
-@pytest.mark.parametrize("prec,rtol", [(W.P64, 1e-12), (W.P32, 1e-7)])
+# sums: an FP32 grid holds J rounded to FP32 and its diagnostics round 1/J
+# and each product Q_v * (1/J) in FP32 (three roundings of 2^-24 relative);
+# the static entry point forms the product in FP64 from FP64 volumes: they
+# agree to within 2^-22 of sum |Q_v| vol
+@pytest.mark.parametrize("prec,rtol", [(W.P64, 1e-12), (W.P32, 2.0 ** -22)])
 def test_static_scratch_diagnostics_match_grid_diagnostics(jz, prec, rtol):
     import torch
 
