@@ -126,14 +126,29 @@ def measured_hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+# stage kernel source files and names per precision (0 P64, 1 P32_M64, 2 P32)
+STAGE_SOURCES = {2: ("jz_stage_v.cu", "jz_stage_common.cuh"),
+                 1: ("jz_stage.cu", "jz_stage_common.cuh"),
+                 0: ("jz_stage.cu", "jz_stage_common.cuh")}
+STAGE_KERNELS = {2: "k_stage_v (fused RK stage, vector node records)",
+                 1: "k_stage<float,double,32,16> (fused RK stage)",
+                 0: "k_stage<double,double,16,16> (fused RK stage)"}
+
+
+def stage_source_sha(prec: int) -> str:
+    h = hashlib.sha256()
+    for name in STAGE_SOURCES[prec]:
+        with open(os.path.join(ROOT, "paper_2003_09926_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def stage_traffic(prec: int):
     """DRAM bytes per point-stage of the stage kernel from a committed ncu
     capture, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2003_09926_gb300", "csrc", "jz_stage.cu")
     p = os.path.join(ROOT, "profiles", "stage_traffic.json")
     try:
-        with open(src, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        sha = stage_source_sha(prec)
         with open(p) as fh:
             rec = json.load(fh)
         ent = rec.get(str(prec))
@@ -438,7 +453,7 @@ def main(argv=None):
     total_ms = sum(prof[0])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tr * pts) if tr else None, "peak_kind": peak_kind,
-                "kernel": "k_stage (fused RK stage)", "algorithmic_bytes_per_point_stage": bpps,
+                "kernel": STAGE_KERNELS[head], "algorithmic_bytes_per_point_stage": bpps,
                 "points_per_launch": pts, "avg_launch_ms": stage_ms,
                 "share_of_step": ms_k / total_ms if total_ms else None,
                 "other_kernels_ms": {"boundary_fill": prof[0][1], "timestep": prof[0][2]}}

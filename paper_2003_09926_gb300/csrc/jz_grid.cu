@@ -315,7 +315,8 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
 }
 
 template <typename ST, typename MT>
-__global__ void k_bc_fill(Layout L, Slabs sl, const double* __restrict__ inflow, FlowC F, ST* __restrict__ Q,
+__global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constant__ Slabs sl,
+                          const double* __restrict__ inflow, const __grid_constant__ FlowC F, ST* __restrict__ Q,
                           const MT* __restrict__ M) {
   fill_slab<ST, MT>(L, sl, blockIdx.y, inflow, F, Q, M);
 }
