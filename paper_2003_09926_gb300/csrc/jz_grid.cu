@@ -210,50 +210,6 @@ __device__ void riemann_farfield(const FlowC& F, const T qi[5], const T n[3], T 
   to_conserved<T>(gm1, rho, ut[0] + un * n[0], ut[1] + un * n[1], ut[2] + un * n[2], p, qb);
 }
 
-// Value of boundary node (i, j, k) (a grid node on at least one non-periodic
-// face): the face latest in the order y-, y+, z-, z+, x+, x- decides; the
-// far field reads the nearest interior node and the face normal from the
-// metric terms at the boundary node.
-template <typename ST, typename MT>
-__device__ void boundary_value(const Layout& L, const double* __restrict__ inflow, const FlowC& F,
-                               const ST* __restrict__ Q, const MT* __restrict__ M, int i, int j, int k, ST qb[5]) {
-  const int order[6] = {2, 3, 4, 5, 1, 0};
-  int idx[3] = {i, j, k};
-  int face = -1;
-  for (int o = 0; o < 6; ++o) {
-    int f = order[o], d = f / 2;
-    if (L.bc[f] == BC_PERIODIC) continue;
-    int target = (f % 2 == 0) ? 0 : L.n[d] - 1;
-    if (idx[d] == target) face = f;
-  }
-  if (L.bc[face] == BC_INFLOW) {  // x- face only: profile tabulated per (j, k)
-    const double u = inflow[(long long)k * L.n[1] + j];
-    to_conserved<ST>((ST)F.gm1, ST(1), (ST)u, ST(0), ST(0), (ST)(1.0 / F.gamma), qb);
-    return;
-  }
-  int ci[3];
-  for (int d = 0; d < 3; ++d) {
-    ci[d] = idx[d];
-    if (!L.per[d]) ci[d] = ci[d] < 1 ? 1 : (ci[d] > L.n[d] - 2 ? L.n[d] - 2 : ci[d]);
-  }
-  long long c = L.at(ci[0], ci[1], ci[2]);
-  ST qi[5];
-  for (int v = 0; v < 5; ++v) qi[v] = Q[(long long)v * L.npad + c];
-  int d = face / 2;
-  long long nb = L.at(i, j, k);
-  ST a = (ST)M[(long long)(3 * d) * L.npad + nb];
-  ST b = (ST)M[(long long)(3 * d + 1) * L.npad + nb];
-  ST cc = (ST)M[(long long)(3 * d + 2) * L.npad + nb];
-  ST sgn = (face % 2 == 0) ? ST(-1) : ST(1);
-  ST inv = sgn / sqrt(a * a + b * b + cc * cc);
-  ST n[3] = {a * inv, b * inv, cc * inv};
-  riemann_farfield<ST>(F, qi, n, qb);
-}
-
-// Boundary fill: every padded node outside the updated box takes the value
-// of the grid node its index maps to (wrap / clamp), and that node, when it
-// is a boundary node, takes its boundary-condition value.  Only interior
-// nodes are read, so the kernel is race-free in one launch.
 // Six boxes covering the padded nodes that lie inside an outer box [ol, oh]
 // but outside an inner box [il, ih] (z slabs over the whole outer plane, y
 // slabs over the inner k range, x slabs over the inner j, k range).
@@ -296,21 +252,90 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
 template <typename ST, typename MT>
 __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
                                           const FlowC& F, ST* __restrict__ Q, const MT* __restrict__ M) {
+  // one node per thread (four per thread with their loads issued together
+  // measured slower: fewer resident threads)
+  constexpr int U = 1;
   const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-    int i, j, k;
-    slab_node(sl, q, t, i, j, k);
-    const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
-    const int mk = map_index(k, L.n[2], L.per[2]);
-    ST v[5];
-    if (mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2]) {
-      const long long src = L.at(mi, mj, mk);
-      for (int c = 0; c < 5; ++c) v[c] = Q[(long long)c * L.npad + src];
-    } else {
-      boundary_value<ST, MT>(L, inflow, F, Q, M, mi, mj, mk, v);
+  const int bw = blockDim.x;
+  for (int tb = blockIdx.x * bw * U + threadIdx.x; tb < tot; tb += gridDim.x * bw * U) {
+    long long dst[U], src[U], nb[U];
+    int kind[U], face[U], inf[U];  // kind: 0 copy, 1 inflow, 2 far field, -1 none
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int i, j, k;
+      kind[u] = -1;
+      face[u] = 0;
+      inf[u] = 0;
+      src[u] = nb[u] = dst[u] = 0;
+      if (!slab_node(sl, q, tb + u * bw, i, j, k)) continue;
+      dst[u] = L.at(i, j, k);
+      const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
+      const int mk = map_index(k, L.n[2], L.per[2]);
+      if (mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2]) {
+        kind[u] = 0;
+        src[u] = L.at(mi, mj, mk);
+        continue;
+      }
+      // boundary node (mi, mj, mk): the face latest in the order y-, y+, z-,
+      // z+, x+, x- decides
+      const int idx[3] = {mi, mj, mk};
+      const int order[6] = {2, 3, 4, 5, 1, 0};
+      int f = -1;
+#pragma unroll
+      for (int o = 0; o < 6; ++o) {
+        const int ff = order[o], d = ff / 2;
+        if (L.bc[ff] == BC_PERIODIC) continue;
+        if (idx[d] == ((ff % 2 == 0) ? 0 : L.n[d] - 1)) f = ff;
+      }
+      face[u] = f;
+      if (L.bc[f] == BC_INFLOW) {  // x- face only: profile tabulated per (j, k)
+        kind[u] = 1;
+        inf[u] = mk * L.n[1] + mj;
+        continue;
+      }
+      kind[u] = 2;  // far field: nearest interior node, normal at the boundary node
+      int ci[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        ci[d] = L.per[d] ? idx[d] : (idx[d] < 1 ? 1 : (idx[d] > L.n[d] - 2 ? L.n[d] - 2 : idx[d]));
+      src[u] = L.at(ci[0], ci[1], ci[2]);
+      nb[u] = L.at(mi, mj, mk);
     }
-    const long long g = L.at(i, j, k);
-    for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + g] = v[c];
+    ST qv[U][5], mv[U][3];
+    double uin[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uin[u] = 0.0;
+      if (kind[u] == 0 || kind[u] == 2) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qv[u][v] = Q[(long long)v * L.npad + src[u]];
+      }
+      if (kind[u] == 2) {
+        const int d = face[u] / 2;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv[u][c] = (ST)M[(long long)(3 * d + c) * L.npad + nb[u]];
+      }
+      if (kind[u] == 1) uin[u] = inflow[inf[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (kind[u] < 0) continue;
+      ST v[5];
+      if (kind[u] == 0) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c] = qv[u][c];
+      } else if (kind[u] == 1) {
+        to_conserved<ST>((ST)F.gm1, ST(1), (ST)uin[u], ST(0), ST(0), (ST)(1.0 / F.gamma), v);
+      } else {
+        const ST a = mv[u][0], b = mv[u][1], cc = mv[u][2];
+        const ST sgn = (face[u] % 2 == 0) ? ST(-1) : ST(1);
+        const ST inv = sgn / sqrt(a * a + b * b + cc * cc);
+        const ST n[3] = {a * inv, b * inv, cc * inv};
+        riemann_farfield<ST>(F, qv[u], n, v);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + dst[u]] = v[c];
+    }
   }
 }
 

@@ -45,6 +45,7 @@ constexpr int TI = 32, TJ = 16;
 constexpr int NTILE = TI * TJ;                  // 512 tile nodes
 constexpr int NJH = 2 * TI, NIH = 2 * TJ;       // j-halo (rows -1, TJ) and i-halo (columns -1, TI) nodes
 constexpr int NT = NTILE + NJH + NIH;           // 608 threads
+constexpr int NCH = 3 * (NJH + NIH);            // plane elements converted by the halo threads
 constexpr int RW = TI + 4, RH = TJ + 4, PL = RW * RH;  // staged plane: tile + two-node halo (36 x 20)
 constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 36 columns
 // ring records: rows padded to 37 so that the column-wise accesses of the
@@ -362,8 +363,11 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     float* qe = sm.QE + s;
     float4* pv = sm.PV + s;
     float* pp = sm.PP + s;
-    // halo threads (lighter elsewhere) take the second round first
-    for (int e = (tid + NJH + NIH) % NT; e < PL; e += NT) {
+    // halo threads (lighter in the node pass) take three elements each, tile
+    // threads one or none
+    const int e0 = tid < NTILE ? NCH + tid : tid - NTILE;
+    const int e1 = tid < NTILE ? PL : NCH, es = tid < NTILE ? NTILE : NJH + NIH;
+    for (int e = e0; e < e1; e += es) {
       const float q0 = src[e], q1 = src[PL + e], q2 = src[2 * PL + e], q3 = src[3 * PL + e], q4 = src[4 * PL + e];
       const float ri = Fn<float>::rcp(q0);
       const float u = q1 * ri, v = q2 * ri, w = q3 * ri;
@@ -450,16 +454,17 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     }
   };
 
-  // i/j residual of this thread's tile node: the high-side faces come from
-  // the neighbours, the low-side j face from registers (keeping the low-side
-  // i face as well would exceed the register budget)
-  auto rij = [&](const float hj[5], float R[5]) {
-    float a[5], b[5], d[5];
+  // i/j residual of this thread's tile node from the four face fluxes
+  // around it (keeping the node's own faces in registers from the face
+  // phase through the next node pass would exceed the register budget)
+  auto rij = [&](float R[5]) {
+    float a[5], b[5], d[5], e[5];
     ld5(sm.Hi4, sm.Hi1, ny * HIW + nx + 1, a);
     ld5(sm.Hi4, sm.Hi1, ny * HIW + nx, d);
     ld5(sm.Hj4, sm.Hj1, (ny + 1) * TI + nx, b);
+    ld5(sm.Hj4, sm.Hj1, ny * TI + nx, e);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) R[v] = (a[v] - d[v]) + (b[v] - hj[v]);
+    for (int v = 0; v < 5; ++v) R[v] = (a[v] - d[v]) + (b[v] - e[v]);
   };
 
   // k face flux between planes ka and ka+1 of this thread's column; q1 is
@@ -497,7 +502,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   float* scr[3] = {reinterpret_cast<float*>(smem + O_SCR), reinterpret_cast<float*>(smem + O_SCR + RAW_B),
                    reinterpret_cast<float*>(smem + O_SCR + 2 * RAW_B)};
 
-  // ---- prologue: planes t0-2 .. t0+1 staged at once, converted
+  // ---- prologue: planes t0-2 .. t0+1 staged at once and converted
   issue_raw(t0 - 2, B_RAW, sm.raw, 0);
   issue_raw(t0 - 1, 1, scr[0], 0);
   issue_raw(t0, 2, scr[1], 0);
@@ -517,76 +522,86 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   {
     float G3m[5], lt3m = 0.f, nu3m = 0.f, Jm = 0.f;
     float G3c[5], lt3c = 0.f, nu3c = 0.f, Jc = 0.f;
-    float Rc[5], hprev[5];
+    float hprev[5];
     Own w;
+    // node pass of plane t0-1 (its k data only), of plane t0, the k face
+    // t0 - 1/2, the i/j faces of plane t0 and the conversion of plane t0+2
     wait(B_MET, met_parity(t0 - 1), t0 - 1);
     node_pass(t0 - 1, w, G3m, lt3m, nu3m, Jm);
     if (__syncthreads_or(!ok)) goto fail;
     issue_met(t0);
     wait(B_MET, met_parity(t0), t0);
     node_pass(t0, w, G3c, lt3c, nu3c, Jc);
+    if (role == 0) {
+      float q1[5];
+      const int s = slot(t0);
+      ld5(sm.QV + s, sm.QE + s, oo, q1);
+      kface(t0 - 1, G3m, G3c, lt3m, lt3c, nu3m, nu3c, q1, hprev);
+    }
     if (__syncthreads_or(!ok)) goto fail;
     issue_met(t0 + 1);
+    issue_q0(t0);
     {
       float hi[5], hj[5], qo[5];
       face_pass(t0, w, hi, hj, qo);
-      if (role == 0) kface(t0 - 1, G3m, G3c, lt3m, lt3c, nu3m, nu3c, qo, hprev);
-      __syncthreads();
-      if (role == 0) rij(hj, Rc);
     }
     // ring slot of plane t0-2 is free: its last readers were the k face above
     wait(B_RAW, raw_parity(t0 + 2), t0 + 2);
     convert(sm.raw, t0 + 2);
     if (__syncthreads_or(!ok)) goto fail;
     if (t0 + 3 <= t1 + 1) issue_raw(t0 + 3, B_RAW, sm.raw, raw_parity(t0 + 3));
-    issue_q0(t0);
 
-    // ---- march in k: iteration t writes plane t
+    // ---- march in k: iteration t writes plane t.  Phase 1: node pass of
+    // plane t+1, k face t + 1/2, i/j residual of plane t (faces from phase 2
+    // of the previous iteration) and the update of plane t.  Phase 2: i/j
+    // faces of plane t+1 and the conversion of plane t+3 (into the ring slot
+    // of plane t-1, whose last reader was the k face of phase 1).
     for (int t = t0; t < t1; ++t) {
       float G3n[5], lt3n = 0.f, nu3n = 0.f, Jn = 0.f;
       wait(B_MET, met_parity(t + 1), t + 1);
       node_pass(t + 1, w, G3n, lt3n, nu3n, Jn);
-      if (__syncthreads_or(!ok)) goto fail;
-      if (t + 2 <= t1) issue_met(t + 2);
-      float hi[5], hj[5], qo[5], hk[5];
-      face_pass(t + 1, w, hi, hj, qo);
-      if (role == 0) kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, qo, hk);
-      __syncthreads();
       if (!q0_ring) wait(B_Q0, (uint32_t)((t - t0) & 1), t);
       if (role == 0) {
-        float Rn[5];
-        rij(hj, Rn);
+        float q1[5], hk[5], R[5];
+        const int s = slot(t + 1);
+        ld5(sm.QV + s, sm.QE + s, oo, q1);
+        kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, q1, hk);
+        rij(R);
         if (own) {
           float q0[5];
           if (q0_ring) {
-            const int s = slot(t);
-            ld5(sm.QV + s, sm.QE + s, oo, q0);
+            const int s0 = slot(t);
+            ld5(sm.QV + s0, sm.QE + s0, oo, q0);
           } else {
 #pragma unroll
             for (int v = 0; v < 5; ++v) q0[v] = q0buf[v * UPL + ny * RW + nx + 2];
           }
           const long long n = n_t0 + (long long)(t - t0) * L.plane;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
+          for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (R[v] + (hk[v] - hprev[v]));
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           G3c[v] = G3n[v];
-          Rc[v] = Rn[v];
           hprev[v] = hk[v];
         }
         lt3c = lt3n;
         nu3c = nu3n;
         Jc = Jn;
       }
-      // plane t+3 takes the ring slot of plane t-1 (last read by the k face)
+      if (__syncthreads_or(!ok)) goto fail;
+      if (t + 2 <= t1) issue_met(t + 2);
+      if (t + 1 < t1) issue_q0(t + 1);
+      if (t + 1 < t1) {
+        float hi[5], hj[5], qo[5];
+        face_pass(t + 1, w, hi, hj, qo);
+      }
       if (t + 3 <= t1 + 1) {
         wait(B_RAW, raw_parity(t + 3), t + 3);
         convert(sm.raw, t + 3);
       }
       if (__syncthreads_or(!ok)) goto fail;
       if (t + 4 <= t1 + 1) issue_raw(t + 4, B_RAW, sm.raw, raw_parity(t + 4));
-      if (t + 1 < t1) issue_q0(t + 1);
     }
   }
   return true;
