@@ -47,6 +47,14 @@ ES = {0: 8, 1: 4, 2: 4}
 MS = {0: 8, 1: 8, 2: 4}
 
 
+# algorithmic flops per point-stage of the fused stage (hand count of the
+# method's formulas, each face flux formed once; add, mul = 1, fma = 2,
+# div / sqrt / pow = 1 each): conversion 15, node gradients 85, Sutherland 6,
+# Smagorinsky 24, stress and heat flux 41, sound speed 1, per-direction node
+# fluxes, radii and sensors 180, three face fluxes 168, residual 25, update 11
+FLOPS_PER_POINT_STAGE = 556
+
+
 def bytes_per_point_stage(prec: int) -> float:
     es, ms = ES[prec], MS[prec]
     full = 15 * es + 10 * ms
@@ -182,32 +190,40 @@ def weak_value(points_per_rank: int, steps: int, ms: float, world: int) -> float
     return world * points_per_rank * 5 * steps / (ms / 1e3) / 1e6
 
 
-def time_steps(jz, torch, g, steps: int, cfl: float, world: int, profile: bool):
-    """Device time of `steps` steps (CUDA events on the grid's stream), max over ranks."""
+def time_steps(jz, torch, g, steps: int, cfl: float, world: int):
+    """Device time of `steps` graph-replayed steps (CUDA events on the grid's
+    stream, barrier and synchronize on both sides), max over ranks."""
     dist = torch.distributed
+    g.nsteps(1, cfl=cfl)  # the step graph is captured before the timed region
     launches0 = jz.jz_launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    if profile:
-        jz.jz_profile_begin(g.h)
     ev0.record(g.stream)
-    for _ in range(steps):
-        g.step(cfl=cfl)
+    g.nsteps(steps, cfl=cfl)
     ev1.record(g.stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = jz.jz_launch_count() - launches0
-    prof = None
-    if profile:
-        prof = jz.jz_profile_read(g.h)
-        jz.jz_profile_end(g.h)
     ms = reduce_max(torch, ms, world, "cuda")
-    return ms, launches, prof
+    return ms, launches
+
+
+def profile_steps(jz, torch, g, steps: int, cfl: float):
+    """Per-kernel-class device times of `steps` steps launched one by one with
+    CUDA events around every launch (outside the timed region):
+    ([ms per class], [launches per class])."""
+    torch.cuda.synchronize()
+    jz.jz_profile_begin(g.h)
+    for _ in range(steps):
+        g.step(cfl=cfl)
+    prof = jz.jz_profile_read(g.h)
+    jz.jz_profile_end(g.h)
+    return prof
 
 
 def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
@@ -224,9 +240,20 @@ def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
     o.step(Q, cfl=cfg["cfl"])
     sec = time.perf_counter() - t0
     pts = interior_points(grid)
+    # the same per-point arithmetic on one core: 3 steps of the 48x32x32 jet
+    c0 = W.config0()
+    oracle.set_threads(1)
+    o1 = oracle.Oracle(c0["grid"], c0["flow"])
+    Q1 = o1.init(c0["seed"])
+    t1 = time.perf_counter()
+    o1.run(Q1, 3, cfl=c0["cfl"])
+    sec1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": pts * 5 / sec / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one RK step (5 stages) of the {sample_shape[0]}x{sample_shape[1]}x{sample_shape[2]} mapped jet "
-                      f"grid in FP64, OpenMP over k-planes, {sec:.1f} s"}
+                      f"grid in FP64, OpenMP over k-planes, {sec:.1f} s",
+            "single_thread": {"value": interior_points(c0["grid"]) * 5 * 3 / sec1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"3 RK steps of the 48x32x32 jet in FP64 on one core, {sec1:.2f} s"}}
 
 
 def bench_batched(jz, torch, W, local: int, steps: int, steps64: int, cfl: float = 0.5):
@@ -371,7 +398,7 @@ def main(argv=None):
     pts = interior_points(grid)
     results = {}
     clocks = None
-    prof = None
+    prof = prof64 = None
     launches = 0
     for prec in (head, W.P32_M64, W.P64):
         g = jz.Grid(dict(grid, precision=prec), device=local).init(cfg["flow"], cfg["seed"] + rank)
@@ -381,10 +408,13 @@ def main(argv=None):
         torch.cuda.synchronize()
         if prec == head:
             with ClockSampler(local) as cs:
-                ms, launches, prof = time_steps(jz, torch, g, steps, cfg["cfl"], world, profile=True)
+                ms, launches = time_steps(jz, torch, g, steps, cfg["cfl"], world)
             clocks = cs.summary()
+            prof = profile_steps(jz, torch, g, 20, cfg["cfl"])
         else:
-            ms, _, _ = time_steps(jz, torch, g, steps, cfg["cfl"], world, profile=False)
+            ms, _ = time_steps(jz, torch, g, steps, cfg["cfl"], world)
+            if prec == W.P64:
+                prof64 = profile_steps(jz, torch, g, 2, cfg["cfl"])
         results[prec] = {"ms_per_step": ms / steps, "steps": steps, "value": weak_value(pts, steps, ms, world)}
         g.close()
         del g
@@ -451,12 +481,26 @@ def main(argv=None):
     achieved = bpps * pts / (stage_ms / 1e3) / 1e9
     tr = stage_traffic(head)
     total_ms = sum(prof[0])
+    stream = torch.cuda.current_stream().cuda_stream
+    fp32_peak = jz.jz_fma_peak(False, stream)
+    fp64_peak = jz.jz_fma_peak(True, stream)
+    fp32_tf = FLOPS_PER_POINT_STAGE * pts / (stage_ms / 1e3) / 1e12
+    stage64_ms = prof64[0][0] / max(1, prof64[1][0])
+    fp64_tf = FLOPS_PER_POINT_STAGE * pts / (stage64_ms / 1e3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tr * pts) if tr else None, "peak_kind": peak_kind,
                 "kernel": STAGE_KERNELS[head], "algorithmic_bytes_per_point_stage": bpps,
                 "points_per_launch": pts, "avg_launch_ms": stage_ms,
                 "share_of_step": ms_k / total_ms if total_ms else None,
-                "other_kernels_ms": {"boundary_fill": prof[0][1], "timestep": prof[0][2]}}
+                "other_kernels_ms": {"boundary_fill": prof[0][1], "timestep": prof[0][2]},
+                "profiled_steps": 20,
+                "fp32_alu": {"flops_per_point_stage": FLOPS_PER_POINT_STAGE, "achieved_tflops": fp32_tf,
+                             "peak_tflops": fp32_peak, "frac": fp32_tf / fp32_peak if fp32_peak else None,
+                             "peak_kind": "measured FP32 FMA chains (jz_fma_peak)"}}
+    fp64_roofline = {"bound": "alu", "kernel": STAGE_KERNELS[W.P64], "achieved": fp64_tf, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": fp64_tf / fp64_peak if fp64_peak else None,
+                     "flops_per_point_stage": FLOPS_PER_POINT_STAGE, "avg_launch_ms": stage64_ms,
+                     "peak_kind": "measured FP64 FMA chains (jz_fma_peak)"}
 
     line = {"metric": METRIC, "value": results[head]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": results[head]["ms_per_step"], "higher_is_better": True,
@@ -465,7 +509,8 @@ def main(argv=None):
                        "grid": [grid["ni"], grid["nj"], grid["nk"]], "points_updated": pts,
                        "precision": "P32", "parallelism": f"{world} independent grid(s), one per GPU",
                        "l2": "inputs larger than L2 (state + metrics 1.0 GB per grid)"},
-            "roofline": roofline, "gpu_launches": launches, "clocks": clocks, "e2e": e2e,
+            "roofline": roofline, "fp64_roofline": fp64_roofline, "gpu_launches": launches, "clocks": clocks,
+            "e2e": e2e,
             "variants": {W.PRECISION_NAMES[p]: r for p, r in results.items()},
             "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
                                    "interior": "nodes at least 3 from every face; far-field face nodes can differ by O(1) where the Riemann condition switches branch (sign of u_n, |u_n| = c) between precisions"},

@@ -194,6 +194,15 @@ int jz_profile_begin(jz_grid* g);
 int jz_profile_read(jz_grid* g, double ms[4], int64_t launches[4]);
 int jz_profile_end(jz_grid* g);
 
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (2 flops per FMA; fp64 = 1: FP64, 0: FP32): eight independent FMA chains
+ * per thread on 8 x 256 threads per SM, timed with CUDA events on `stream`
+ * (cudaStream_t as void*; synchronised), best of three after a warm-up.  The
+ * denominator of the FP64 stage kernel's roofline (bound by the FP64 pipe)
+ * and of the FP32 kernel's arithmetic rate.  JZ_EINVAL for a null output or
+ * another fp64 value, JZ_ECUDA on a CUDA error. */
+int jz_fma_peak(int fp64, double* tflops, void* stream);
+
 /* Tile shape of the fused stage kernel for this grid (for tuning and for
  * the batched tile table): ti x tj nodes per CTA, kc planes per CTA chunk.
  * jz_set_tiling may change kc (planes per chunk, >= 1); the tile shape is

@@ -81,6 +81,7 @@ def lib() -> C.CDLL:
             "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "jz_set_tiling": ([G, C.c_int], C.c_int),
             "jz_set_stage_variant": ([G, C.c_int], C.c_int),
+            "jz_fma_peak": ([C.c_int, C.POINTER(C.c_double), VP], C.c_int),
         }
         sig["jz_state_diagnostics_static"] = ([C.c_longlong, C.c_int, VP, VP, C.c_double, VP, VP], C.c_int)
         for name, (args, res) in sig.items():
@@ -217,6 +218,13 @@ def jz_set_tiling(h, kc: int) -> None:
 
 def jz_set_stage_variant(h, variant: int) -> None:
     _check(lib().jz_set_stage_variant(h, variant))
+
+
+def jz_fma_peak(fp64: bool, stream: int = 0) -> float:
+    """Measured FMA throughput of the current device, TFLOP/s."""
+    out = C.c_double(0.0)
+    _check(lib().jz_fma_peak(1 if fp64 else 0, C.byref(out), C.c_void_p(stream)))
+    return out.value
 
 
 def jz_state_diagnostics_static(n_nodes: int, fp64: bool, q_ptr: int, vol_ptr: int, gamma: float, out_ptr: int,
