@@ -131,6 +131,22 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
 /* Release the handle (and any captured graph).  Does not free dev_buf. */
 int jz_grid_destroy(jz_grid* g);
 
+/* --- blocks of a grid (the paper's domain decomposition, Section 4.2) -----
+ * A block holds the nodes [o0[d], o1[d]] (inclusive, d = i, j, k) of the grid
+ * `desc` describes, with its own two ghost layers: every jz_grid entry point
+ * accepts it and acts on those nodes (jz_state_init gives them the values of
+ * the same nodes of the whole grid: the noise is keyed to global indices;
+ * jz_state_download / upload and jz_diagnostics cover the block's nodes).  A
+ * face of the block inside the grid is an exchange face: its first / last
+ * node is updated like an interior node and its ghosts are copies of the
+ * neighbouring block's nodes, filled by the halo exchange of a block set
+ * (jz_blocks_create).  Periodic directions cannot be split; a block has at
+ * least three nodes along a split direction; coordinates and metrics are
+ * those of the whole grid at the same nodes.  JZ_EINVAL for a bad range. */
+int jz_block_bytes(const jz_grid_desc* desc, const int o0[3], const int o1[3], size_t* bytes);
+int jz_block_create(const jz_grid_desc* desc, const int o0[3], const int o1[3], void* dev_buf, size_t bytes,
+                    void* stream, jz_grid** out);
+
 /* Set the flow parameters and enqueue the initial state (JZ_IC_JET: top-hat
  * profile plus noise drawn from SplitMix64(seed ^ (3 lin + m)); or air at
  * rest), then the boundary conditions.  Resets time and step to 0. */
@@ -178,6 +194,20 @@ int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, v
 /* Enqueue n steps of every grid in the batch (graph-captured; asynchronous). */
 int jz_batch_nsteps(jz_batch* b, int n, double cfl);
 int jz_batch_destroy(jz_batch* b);
+
+/* A block set: the blocks of one grid (jz_block_create) stepped together as a
+ * batch whose members are coupled as the paper's decomposed domain is
+ * (Section 4.2): after every stage the ghosts behind each exchange face take
+ * the neighbouring block's nodes (halo exchange on the device, direction by
+ * direction), and every step takes the one time step of the whole grid (the
+ * largest rate over the blocks).  The blocks must partition the grid's nodes
+ * as a tensor product of ranges (every exchange face is shared whole with one
+ * neighbour) and share one description and precision; JZ_EINVAL otherwise.
+ * Each block's nodes then evolve bitwise as the same nodes of the whole grid
+ * stepped alone.  Sized by jz_blocks_bytes; stepped by jz_batch_nsteps (CFL
+ * only); released by jz_batch_destroy. */
+int jz_blocks_bytes(jz_grid* const* blocks, int n, size_t* bytes);
+int jz_blocks_create(jz_grid* const* blocks, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out);
 
 /* --- measurement helpers -------------------------------------------------- */
 

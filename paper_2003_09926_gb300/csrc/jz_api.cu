@@ -86,19 +86,43 @@ static int validate(const jz_grid_desc* d) {
   return JZ_OK;
 }
 
-static Carve carve(const jz_grid_desc* d) {
+// Nodes [o0, o1] of the grid d (the whole grid when o0 is null): a face of
+// the block that lies inside the grid is an exchange face, whose first /
+// last node is updated and whose ghosts are filled by the halo exchange.
+// Block [o0, o1] of the grid d: inside the grid, not split across a periodic
+// direction, and at least three nodes deep along a split direction (its
+// neighbours copy two layers of its nodes into their ghosts)
+static int validate_block(const jz_grid_desc* d, const int* o0, const int* o1) {
+  if (!o0 || !o1) return fail(JZ_EINVAL, "null block range");
+  const int gn[3] = {d->ni, d->nj, d->nk};
+  for (int a = 0; a < 3; ++a) {
+    if (o0[a] < 0 || o1[a] > gn[a] - 1 || o1[a] < o0[a])
+      return fail(JZ_EINVAL, "direction %d: block range [%d, %d] outside the grid's [0, %d]", a, o0[a], o1[a],
+                  gn[a] - 1);
+    const bool split = o0[a] > 0 || o1[a] < gn[a] - 1;
+    if (split && d->bc[2 * a] == JZ_BC_PERIODIC) return fail(JZ_EINVAL, "direction %d: a periodic direction cannot be split", a);
+    if (split && o1[a] - o0[a] + 1 < 3)
+      return fail(JZ_EINVAL, "direction %d: a block of a split direction needs at least 3 nodes", a);
+  }
+  return JZ_OK;
+}
+
+static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1 = nullptr) {
   Carve c;
   Layout& L = c.L;
-  L.n[0] = d->ni; L.n[1] = d->nj; L.n[2] = d->nk;
-  for (int f = 0; f < 6; ++f) L.bc[f] = d->bc[f];
+  const int gn[3] = {d->ni, d->nj, d->nk};
   for (int a = 0; a < 3; ++a) {
+    const int b0 = o0 ? o0[a] : 0, b1 = o1 ? o1[a] : gn[a] - 1;
+    L.n[a] = b1 - b0 + 1;
     L.per[a] = d->bc[2 * a] == JZ_BC_PERIODIC;
-    L.lo[a] = L.per[a] ? 0 : 1;
-    L.hi[a] = L.per[a] ? L.n[a] - 1 : L.n[a] - 2;
+    L.bc[2 * a] = b0 > 0 ? BC_EXCHANGE : d->bc[2 * a];
+    L.bc[2 * a + 1] = b1 < gn[a] - 1 ? BC_EXCHANGE : d->bc[2 * a + 1];
+    L.lo[a] = (L.per[a] || L.bc[2 * a] == BC_EXCHANGE) ? 0 : 1;
+    L.hi[a] = (L.per[a] || L.bc[2 * a + 1] == BC_EXCHANGE) ? L.n[a] - 1 : L.n[a] - 2;
   }
-  L.pitch = ((d->ni + 2 * NG) + 31) / 32 * 32;
-  L.plane = (long long)L.pitch * (d->nj + 2 * NG);
-  L.npad = L.plane * (d->nk + 2 * NG);
+  L.pitch = ((L.n[0] + 2 * NG) + 31) / 32 * 32;
+  L.plane = (long long)L.pitch * (L.n[1] + 2 * NG);
+  L.npad = L.plane * (L.n[2] + 2 * NG);
   c.es = d->precision == JZ_P64 ? 8 : 4;
   c.ms = d->precision == JZ_P32 ? 4 : 8;
   c.tab_len = 0;
@@ -124,7 +148,8 @@ struct EventPair { cudaEvent_t a, b; int cls; };
 using namespace jz;
 
 struct jz_grid {
-  jz_grid_desc desc;
+  jz_grid_desc desc;     // of the whole grid (a block: the grid it is part of)
+  int o0[3], o1[3];      // the nodes of that grid held here (the whole grid: 0 .. n-1)
   jz_flow_params flow;
   bool have_flow = false;
   cudaStream_t stream = nullptr;
@@ -144,6 +169,9 @@ struct jz_grid {
 
 struct jz_batch {
   std::vector<jz_grid*> grids;
+  bool coupled = false;         // blocks of one grid: halo exchange and one time step
+  size_t off_x = 0;             // exchange entries, ordered by direction
+  int xbegin[3] = {0, 0, 0}, xcount[3] = {0, 0, 0}, xblocks = 1;
   cudaStream_t stream = nullptr;
   int prec = 0;
   char* dev = nullptr;
@@ -265,6 +293,11 @@ int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int f
 
 }  // namespace
 
+namespace {
+int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* dev_buf, size_t bytes, void* stream,
+                jz_grid** out);
+}  // namespace
+
 extern "C" {
 
 int jz_last_error(char* buf, size_t len) {
@@ -284,12 +317,38 @@ int jz_grid_bytes(const jz_grid_desc* desc, size_t* bytes) {
   return JZ_OK;
 }
 
+int jz_block_bytes(const jz_grid_desc* desc, const int o0[3], const int o1[3], size_t* bytes) {
+  int rc = validate(desc);
+  if (!rc) rc = validate_block(desc, o0, o1);
+  if (rc) return rc;
+  if (!bytes) return fail(JZ_EINVAL, "null output");
+  *bytes = carve(desc, o0, o1).total;
+  return JZ_OK;
+}
+
 int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* stream, jz_grid** out) {
+  return create_grid(desc, nullptr, nullptr, dev_buf, bytes, stream, out);
+}
+
+int jz_block_create(const jz_grid_desc* desc, const int o0[3], const int o1[3], void* dev_buf, size_t bytes,
+                    void* stream, jz_grid** out) {
+  int rc = validate(desc);
+  if (!rc) rc = validate_block(desc, o0, o1);
+  if (rc) return rc;
+  return create_grid(desc, o0, o1, dev_buf, bytes, stream, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* dev_buf, size_t bytes, void* stream,
+                jz_grid** out) {
   int rc = validate(desc);
   if (rc) return rc;
   if (!out) return fail(JZ_EINVAL, "null output");
   *out = nullptr;
-  Carve cv = carve(desc);
+  Carve cv = carve(desc, o0, o1);
   if (!dev_buf) return fail(JZ_EINVAL, "null device buffer");
   if (((uintptr_t)dev_buf & 255) != 0) return fail(JZ_EINVAL, "device buffer must be 256-byte aligned");
   if (bytes < cv.total) return fail(JZ_ENOMEM, "device buffer holds %zu bytes, grid needs %zu", bytes, cv.total);
@@ -301,6 +360,10 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   jz_grid* g = new (std::nothrow) jz_grid();
   if (!g) return fail(JZ_ENOMEM, "host allocation failed");
   g->desc = *desc;
+  for (int a = 0; a < 3; ++a) {
+    g->o0[a] = o0 ? o0[a] : 0;
+    g->o1[a] = o1 ? o1[a] : (a == 0 ? desc->ni : a == 1 ? desc->nj : desc->nk) - 1;
+  }
   g->stream = (cudaStream_t)stream;
   g->cv = cv;
   g->base = (char*)dev_buf;
@@ -316,6 +379,11 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   d.inflow = (double*)(g->base + cv.off_inflow);
   d.kc = default_kc(cv.L, d.prec);
   d.variant = d.prec == JZ_P32 ? 2 : 0;  // P32: the vector-record kernel (fastest measured)
+  const int gn[3] = {desc->ni, desc->nj, desc->nk};
+  for (int a = 0; a < 3; ++a) {
+    d.goff[a] = g->o0[a];
+    d.gn[a] = gn[a];
+  }
   memset(&d.F, 0, sizeof(d.F));
   // coordinate tables
   double* tab = (double*)(g->base + cv.off_tab);
@@ -330,6 +398,8 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   TabParams tp;
   for (int a = 0; a < 3; ++a) {
     tp.n[a] = cv.L.n[a];
+    tp.off[a] = d.goff[a];
+    tp.gn[a] = d.gn[a];
     tp.per[a] = cv.L.per[a];
     tp.lo[a] = desc->lo[a];
     tp.hi[a] = desc->hi[a];
@@ -364,6 +434,10 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
   *out = g;
   return JZ_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int jz_grid_destroy(jz_grid* g) {
   if (!g) return JZ_OK;
@@ -479,7 +553,8 @@ int jz_diagnostics(jz_grid* g, jz_diag* out) {
 }
 
 static size_t state_count(const jz_grid* g) {
-  return 5ULL * (size_t)g->desc.ni * (size_t)g->desc.nj * (size_t)g->desc.nk;
+  const Layout& L = g->dev.L;  // the grid's (a block's) own nodes
+  return 5ULL * (size_t)L.n[0] * (size_t)L.n[1] * (size_t)L.n[2];
 }
 
 int jz_state_download(jz_grid* g, double* host, size_t n) {
@@ -578,8 +653,10 @@ int jz_set_tiling(jz_grid* g, int kc) {
 namespace {
 
 struct BatchPlan {
-  size_t off_stage, off_bc, off_rate, off_items, off_queue, total;
+  size_t off_stage, off_bc, off_rate, off_items, off_queue, off_x, total;
   std::vector<int4> items;
+  std::vector<XEntry> xs;  // halo exchange (blocks of one grid)
+  int xbegin[3] = {0, 0, 0}, xcount[3] = {0, 0, 0}, xblocks = 1;
 };
 
 // Work items (grid, tile x, tile y, k-chunk) of every grid, largest first,
@@ -619,14 +696,92 @@ int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
   P.off_rate = off; off = align256(off + (size_t)n * rate_ctx_bytes());
   P.off_items = off; off = align256(off + P.items.size() * sizeof(int4));
   P.off_queue = off; off = align256(off + sizeof(unsigned int));
+  P.off_x = off; off = align256(off + P.xs.size() * sizeof(XEntry));
   P.total = off;
+  return JZ_OK;
+}
+
+// Blocks of one grid: same grid description, a partition of its nodes, and
+// for every exchange face exactly one neighbour sharing the face over the
+// same node ranges.  Fills the exchange entries (direction order) and then
+// the batch plan.
+int blocks_plan(jz_grid* const* grids, int n, BatchPlan& P) {
+  if (!grids || n < 1) return fail(JZ_EINVAL, "bad block-set arguments");
+  for (int k = 0; k < n; ++k)
+    if (int rc = check_grid(grids[k], true)) return rc;
+  const jz_grid_desc& G = grids[0]->desc;
+  const int gn[3] = {G.ni, G.nj, G.nk};
+  long long nodes = 0;
+  for (int k = 0; k < n; ++k) {
+    if (memcmp(&grids[k]->desc, &G, sizeof(G)) != 0) return fail(JZ_EINVAL, "blocks %d and 0 describe different grids", k);
+    long long v = 1;
+    for (int a = 0; a < 3; ++a) v *= grids[k]->o1[a] - grids[k]->o0[a] + 1;
+    nodes += v;
+  }
+  if (nodes != (long long)gn[0] * gn[1] * gn[2]) return fail(JZ_EINVAL, "the blocks do not partition the grid's nodes");
+  std::vector<XEntry> byd[3];
+  long long biggest = 1;
+  for (int k = 0; k < n; ++k) {
+    const jz_grid* A = grids[k];
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side) {
+        if (A->dev.L.bc[2 * d + side] != BC_EXCHANGE) continue;
+        // the neighbour starts right after A (side 1) or ends right before it (side 0)
+        int found = -1;
+        for (int m = 0; m < n && found < 0; ++m) {
+          const jz_grid* B = grids[m];
+          bool ok = side ? B->o0[d] == A->o1[d] + 1 : B->o1[d] == A->o0[d] - 1;
+          for (int e = 0; e < 3 && ok; ++e)
+            if (e != d) ok = B->o0[e] == A->o0[e] && B->o1[e] == A->o1[e];
+          if (ok) found = m;
+        }
+        if (found < 0)
+          return fail(JZ_EINVAL, "block %d: no neighbour shares its face %d%c over the same node ranges", k, d,
+                      side ? '+' : '-');
+        const jz_grid* B = grids[found];
+        XEntry x;
+        memset(&x, 0, sizeof(x));
+        x.dq[0] = A->dev.Q0; x.dq[1] = A->dev.QA; x.dq[2] = A->dev.QB;
+        x.sq[0] = B->dev.Q0; x.sq[1] = B->dev.QA; x.sq[2] = B->dev.QB;
+        x.dpitch = A->dev.L.pitch; x.dplane = A->dev.L.plane; x.dnpad = A->dev.L.npad;
+        x.spitch = B->dev.L.pitch; x.splane = B->dev.L.plane; x.snpad = B->dev.L.npad;
+        x.d = d;
+        x.dfirst = side ? A->dev.L.n[d] : -NG;
+        x.sfirst = side ? 0 : B->dev.L.n[d] - NG;
+        const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+        x.ea = A->dev.L.n[e1] + 2 * NG;
+        x.eb = A->dev.L.n[e2] + 2 * NG;
+        biggest = std::max(biggest, 10LL * x.ea * x.eb);
+        byd[d].push_back(x);
+      }
+  }
+  P.xs.clear();
+  for (int d = 0; d < 3; ++d) {
+    P.xbegin[d] = (int)P.xs.size();
+    P.xcount[d] = (int)byd[d].size();
+    P.xs.insert(P.xs.end(), byd[d].begin(), byd[d].end());
+  }
+  P.xblocks = (int)std::min<long long>((biggest + 255) / 256, 1024);
+  return batch_plan(grids, n, P);
+}
+
+// halo exchange of state copy `which` between the blocks of a block set
+int enqueue_exchange(jz_batch* b, int which) {
+  for (int d = 0; d < 3; ++d) {
+    cudaError_t e = launch_exchange(b->prec, b->dev + b->off_x, b->xbegin[d], b->xcount[d], b->xblocks, which, b->stream);
+    if (e != cudaSuccess) return fail(JZ_ECUDA, "halo exchange launch failed: %s", cudaGetErrorString(e));
+  }
   return JZ_OK;
 }
 
 int enqueue_batch_step(jz_batch* b, double cfl) {
   const int n = (int)b->grids.size();
   cudaStream_t s = b->stream;
-  cudaError_t e = launch_timestep_batch(b->prec, b->dev + b->off_rate, n, cfl, s);
+  // blocks of one grid: Q^n's ghosts behind exchange faces first (its
+  // boundary nodes and boundary ghosts are set by the previous fill)
+  if (b->coupled)
+    if (int rc = enqueue_exchange(b, 0)) return rc;
+  cudaError_t e = launch_timestep_batch(b->prec, b->dev + b->off_rate, n, cfl, b->coupled, s);
   if (e != cudaSuccess) return fail(JZ_ECUDA, "batched time step launch failed: %s", cudaGetErrorString(e));
   const int src[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
   for (int l = 0; l < 5; ++l) {
@@ -635,7 +790,55 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
     e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched boundary launch failed: %s", cudaGetErrorString(e));
+    if (b->coupled && l < 4)
+      if (int rc = enqueue_exchange(b, out[l])) return rc;
   }
+  return JZ_OK;
+}
+
+// A batch (independent grids) or a block set (coupled: blocks of one grid).
+int create_batch(jz_grid* const* grids, int n, bool coupled, void* dev_buf, size_t bytes, void* stream,
+                 jz_batch** out) {
+  if (!out) return fail(JZ_EINVAL, "null output");
+  *out = nullptr;
+  BatchPlan P;
+  if (int rc = coupled ? blocks_plan(grids, n, P) : batch_plan(grids, n, P)) return rc;
+  if (!dev_buf || ((uintptr_t)dev_buf & 255)) return fail(JZ_EINVAL, "batch buffer must be non-null and 256-byte aligned");
+  if (bytes < P.total) return fail(JZ_ENOMEM, "batch buffer holds %zu bytes, batch needs %zu", bytes, P.total);
+  const int prec = grids[0]->dev.prec;
+  std::vector<char> host(P.total, 0);
+  int nb = 1;
+  for (int k = 0; k < n; ++k) {
+    stage_ctx_fill(host.data() + P.off_stage + (size_t)k * stage_ctx_bytes(prec), grids[k]->dev);
+    int a = 1;
+    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a);
+    nb = std::max(nb, a);
+    rate_ctx_fill(host.data() + P.off_rate + (size_t)k * rate_ctx_bytes(), grids[k]->dev);
+  }
+  memcpy(host.data() + P.off_items, P.items.data(), P.items.size() * sizeof(int4));
+  if (!P.xs.empty()) memcpy(host.data() + P.off_x, P.xs.data(), P.xs.size() * sizeof(XEntry));
+  JZ_CUDA(cudaMemcpy(dev_buf, host.data(), P.total, cudaMemcpyHostToDevice));
+  jz_batch* b = new (std::nothrow) jz_batch();
+  if (!b) return fail(JZ_ENOMEM, "host allocation failed");
+  b->grids.assign(grids, grids + n);
+  b->stream = (cudaStream_t)stream;
+  b->prec = prec;
+  b->dev = (char*)dev_buf;
+  b->off_stage = P.off_stage;
+  b->off_bc = P.off_bc;
+  b->off_rate = P.off_rate;
+  b->off_items = P.off_items;
+  b->off_queue = P.off_queue;
+  b->nitems = (int)P.items.size();
+  b->bc_blocks = nb;
+  b->coupled = coupled;
+  b->off_x = P.off_x;
+  for (int d = 0; d < 3; ++d) {
+    b->xbegin[d] = P.xbegin[d];
+    b->xcount[d] = P.xcount[d];
+  }
+  b->xblocks = P.xblocks;
+  *out = b;
   return JZ_OK;
 }
 
@@ -652,39 +855,19 @@ int jz_batch_bytes(jz_grid* const* grids, int n, size_t* bytes) {
 }
 
 int jz_batch_create(jz_grid* const* grids, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out) {
-  if (!out) return fail(JZ_EINVAL, "null output");
-  *out = nullptr;
+  return create_batch(grids, n, false, dev_buf, bytes, stream, out);
+}
+
+int jz_blocks_bytes(jz_grid* const* blocks, int n, size_t* bytes) {
+  if (!bytes) return fail(JZ_EINVAL, "null output");
   BatchPlan P;
-  if (int rc = batch_plan(grids, n, P)) return rc;
-  if (!dev_buf || ((uintptr_t)dev_buf & 255)) return fail(JZ_EINVAL, "batch buffer must be non-null and 256-byte aligned");
-  if (bytes < P.total) return fail(JZ_ENOMEM, "batch buffer holds %zu bytes, batch needs %zu", bytes, P.total);
-  const int prec = grids[0]->dev.prec;
-  std::vector<char> host(P.total, 0);
-  int nb = 1;
-  for (int k = 0; k < n; ++k) {
-    stage_ctx_fill(host.data() + P.off_stage + (size_t)k * stage_ctx_bytes(prec), grids[k]->dev);
-    int a = 1;
-    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a);
-    nb = std::max(nb, a);
-    rate_ctx_fill(host.data() + P.off_rate + (size_t)k * rate_ctx_bytes(), grids[k]->dev);
-  }
-  memcpy(host.data() + P.off_items, P.items.data(), P.items.size() * sizeof(int4));
-  JZ_CUDA(cudaMemcpy(dev_buf, host.data(), P.total, cudaMemcpyHostToDevice));
-  jz_batch* b = new (std::nothrow) jz_batch();
-  if (!b) return fail(JZ_ENOMEM, "host allocation failed");
-  b->grids.assign(grids, grids + n);
-  b->stream = (cudaStream_t)stream;
-  b->prec = prec;
-  b->dev = (char*)dev_buf;
-  b->off_stage = P.off_stage;
-  b->off_bc = P.off_bc;
-  b->off_rate = P.off_rate;
-  b->off_items = P.off_items;
-  b->off_queue = P.off_queue;
-  b->nitems = (int)P.items.size();
-  b->bc_blocks = nb;
-  *out = b;
+  if (int rc = blocks_plan(blocks, n, P)) return rc;
+  *bytes = P.total;
   return JZ_OK;
+}
+
+int jz_blocks_create(jz_grid* const* blocks, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out) {
+  return create_batch(blocks, n, true, dev_buf, bytes, stream, out);
 }
 
 int jz_batch_nsteps(jz_batch* b, int n, double cfl) {

@@ -70,6 +70,7 @@ struct Scalars {
   long long step;     // completed steps
   double cfl;         // CFL number of the current step (0 = fixed dt)
   double dt_fixed;    // fixed time step when cfl == 0
+  double rate;        // this grid's largest stable-step rate (blocks of one grid: combined over the blocks)
   unsigned int count; // last-block counter of the time-step reduction
   unsigned int dcount;// last-block counter of the diagnostics reduction
   int err;            // sticky device error flag
@@ -81,8 +82,11 @@ constexpr int RED_BLOCKS = 1216;  // fixed grid of the reductions (8 x 152 SMs)
 constexpr int RED_THREADS = 256;
 constexpr int DIAG_WORDS = 11;    // per-block diagnostics partial
 
-// Face kinds
-enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2 };
+// Face kinds.  BC_EXCHANGE marks a face of a block of a larger grid that lies
+// inside that grid: its ghost layers are copies of the neighbouring block's
+// nodes (halo exchange), and its first / last node is updated like any
+// interior node.
+enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2, BC_EXCHANGE = 3 };
 
 __host__ __device__ __forceinline__ int map_index(int idx, int n, int periodic) {
   if (periodic) { int r = idx % n; return r < 0 ? r + n : r; }

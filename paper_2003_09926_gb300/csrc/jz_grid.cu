@@ -25,8 +25,9 @@ __device__ double stretch_g(const TabParams& p, double H, double s) {
   return s - (p.stretch_c / H) * (tanh((H * s - p.cluster_r) / p.stretch_w) + tanh((H * s + p.cluster_r) / p.stretch_w));
 }
 
+// coordinate at global index idx along direction d
 __device__ double base_coord(const TabParams& p, int d, double idx) {
-  int n = p.n[d];
+  int n = p.gn[d];
   double lo = p.lo[d], hi = p.hi[d];
   if (p.per[d]) return lo + (hi - lo) * idx / n;
   if (d == 0 || p.stretch_c == 0.0) return lo + (hi - lo) * idx / (n - 1);
@@ -47,18 +48,18 @@ __global__ void k_tables(TabParams p, double* tab) {
     for (int d = 0; d < 3; ++d) {
       long long len = p.n[d] + 2 * NG;
       if (t >= base_off[d] && t < base_off[d] + len) {
-        int idx = (int)(t - base_off[d]) - NG;
+        int idx = (int)(t - base_off[d]) - NG + p.off[d];
         tab[t] = base_coord(p, d, idx);
       }
       if (t >= h_off[d] && t < h_off[d] + len) {
-        int idx = (int)(t - h_off[d]) - NG;
+        int idx = (int)(t - h_off[d]) - NG + p.off[d];
         tab[t] = 0.5 * (base_coord(p, d, idx + 1.0) - base_coord(p, d, idx - 1.0));
       }
       for (int e = 0; e < 3; ++e) {
         long long le = p.n[e] + 2 * NG;
         if (t >= sn_off[d][e] && t < sn_off[d][e] + le) {
-          int idx = (int)(t - sn_off[d][e]) - NG;
-          int P = p.per[e] ? p.n[e] : p.n[e] - 1;
+          int idx = (int)(t - sn_off[d][e]) - NG + p.off[e];
+          int P = p.per[e] ? p.gn[e] : p.gn[e] - 1;
           tab[t] = sin(2.0 * kPi * p.m[3 * d + e] * idx / P + p.th[3 * d + e]);
         }
       }
@@ -70,13 +71,16 @@ __global__ void k_tables(TabParams p, double* tab) {
 // metric terms (conservative form) and Jacobian, FP64 arithmetic
 // ---------------------------------------------------------------------------
 
+// Over the local box [a, b]: the grid nodes, plus the first ghost layer
+// behind a face of a block that lies inside the larger grid (the stage
+// kernel reads the metrics of its one-node halo there).
 template <typename MT>
-__global__ void k_metrics(Layout L, Coords C, MT* __restrict__ M) {
-  long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+__global__ void k_metrics(Layout L, Coords C, MT* __restrict__ M, int a0, int a1, int a2, int b0, int b1, int b2) {
+  const long long E0 = b0 - a0 + 1, E1 = b1 - a1 + 1, N = E0 * E1 * (b2 - a2 + 1);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t % L.n[0]);
-    int j = (int)((t / L.n[0]) % L.n[1]);
-    int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    int i = a0 + (int)(t % E0);
+    int j = a1 + (int)((t / E0) % E1);
+    int k = a2 + (int)(t / (E0 * E1));
     const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     auto X = [&](int m, int di, int dj, int dk) { return C.x(m, i + di, j + dj, k + dk); };
     // D_b x_p at the node shifted by o: half the difference across direction b
@@ -268,6 +272,11 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
       inf[u] = 0;
       src[u] = nb[u] = dst[u] = 0;
       if (!slab_node(sl, q, tb + u * bw, i, j, k)) continue;
+      // ghosts behind a face inside a larger grid are the halo exchange's
+      if ((i < 0 && L.bc[0] == BC_EXCHANGE) || (i >= L.n[0] && L.bc[1] == BC_EXCHANGE) ||
+          (j < 0 && L.bc[2] == BC_EXCHANGE) || (j >= L.n[1] && L.bc[3] == BC_EXCHANGE) ||
+          (k < 0 && L.bc[4] == BC_EXCHANGE) || (k >= L.n[2] && L.bc[5] == BC_EXCHANGE))
+        continue;
       dst[u] = L.at(i, j, k);
       const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
       const int mk = map_index(k, L.n[2], L.per[2]);
@@ -284,7 +293,7 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
 #pragma unroll
       for (int o = 0; o < 6; ++o) {
         const int ff = order[o], d = ff / 2;
-        if (L.bc[ff] == BC_PERIODIC) continue;
+        if (L.bc[ff] == BC_PERIODIC || L.bc[ff] == BC_EXCHANGE) continue;
         if (idx[d] == ((ff % 2 == 0) ? 0 : L.n[d] - 1)) f = ff;
       }
       face[u] = f;
@@ -293,11 +302,10 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
         inf[u] = mk * L.n[1] + mj;
         continue;
       }
-      kind[u] = 2;  // far field: nearest interior node, normal at the boundary node
+      kind[u] = 2;  // far field: nearest updated node, normal at the boundary node
       int ci[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        ci[d] = L.per[d] ? idx[d] : (idx[d] < 1 ? 1 : (idx[d] > L.n[d] - 2 ? L.n[d] - 2 : idx[d]));
+      for (int d = 0; d < 3; ++d) ci[d] = idx[d] < L.lo[d] ? L.lo[d] : (idx[d] > L.hi[d] ? L.hi[d] : idx[d]);
       src[u] = L.at(ci[0], ci[1], ci[2]);
       nb[u] = L.at(mi, mj, mk);
     }
@@ -362,6 +370,38 @@ __global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
   fill_slab<ST, MT>(X.L, X.fill, blockIdx.y, X.inflow, X.F, (ST*)X.Q[which], (const MT*)X.M);
 }
 
+// Halo exchange between blocks of one grid (the paper's ghost exchange,
+// Section 4.2, between blocks on one device): each entry copies the two node
+// layers of block src next to a shared face into the two ghost layers of
+// block dst behind it, over the padded extents of the other two directions.
+// One launch per direction, in the order i, j, k, so that edge and corner
+// ghosts take values already exchanged in the earlier directions.
+template <typename ST>
+__global__ void k_exchange(const XEntry* __restrict__ xs, int which) {
+  const XEntry& X = xs[blockIdx.y];
+  const int d = X.d, e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  const long long per_var = 2LL * X.ea * X.eb;
+  const long long tot = 5 * per_var;
+  ST* dq = (ST*)X.dq[which];
+  const ST* sq = (const ST*)X.sq[which];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / per_var);
+    long long r = t - v * per_var;
+    const int a = (int)(r % X.ea) - NG;  // fastest: direction e1
+    r /= X.ea;
+    const int b = (int)(r % X.eb) - NG;
+    const int l = (int)(r / X.eb);
+    int di[3], si[3];
+    di[d] = X.dfirst + l;
+    si[d] = X.sfirst + l;
+    di[e1] = si[e1] = a;
+    di[e2] = si[e2] = b;
+    const long long dofs = (di[0] + NG) + (di[1] + NG) * X.dpitch + (di[2] + NG) * X.dplane;
+    const long long sofs = (si[0] + NG) + (si[1] + NG) * X.spitch + (si[2] + NG) * X.splane;
+    dq[v * X.dnpad + dofs] = sq[v * X.snpad + sofs];
+  }
+}
+
 // axial inflow velocity of the jet profile at the x- face nodes (FP64, once per state_init)
 __global__ void k_inflow(Layout L, Coords C, FlowC F, double* __restrict__ inflow) {
   const int n = L.n[1] * L.n[2];
@@ -376,8 +416,12 @@ __global__ void k_inflow(Layout L, Coords C, FlowC F, double* __restrict__ inflo
 // initial state (jet column plus seeded noise, or air at rest)
 // ---------------------------------------------------------------------------
 
+// The noise of a node is keyed to its global linear index (goff: global index
+// of local node 0, gn: global node counts), so a block of a larger grid gets
+// the values of the same nodes of the whole grid.
 template <typename ST>
-__global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restrict__ Q) {
+__global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restrict__ Q, int go0, int go1, int go2,
+                       int gn0, int gn1) {
   long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
     int i = (int)(t % L.n[0]);
@@ -387,7 +431,7 @@ __global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restric
     if (F.ic == JZ_IC_JET) {
       double y = C.x(1, i, j, k), z = C.x(2, i, j, k);
       u[0] = jet_profile(F, sqrt(y * y + z * z));
-      uint64_t lin = (uint64_t)t;  // i + ni (j + nj k)
+      const uint64_t lin = (uint64_t)(i + go0) + (uint64_t)gn0 * ((uint64_t)(j + go1) + (uint64_t)gn1 * (uint64_t)(k + go2));
       for (int m = 0; m < 3; ++m) {
         double xi = unit53(splitmix64(seed ^ (3ULL * lin + (uint64_t)m)));
         u[m] += F.noise * F.mach * (2.0 * xi - 1.0);
@@ -455,14 +499,19 @@ cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s) {
 }
 
 cudaError_t launch_metrics(const GridDev& g, cudaStream_t s) {
-  long long N = (long long)g.L.n[0] * g.L.n[1] * g.L.n[2];
-  int zero[3] = {0, 0, 0}, top[3] = {g.L.n[0] - 1, g.L.n[1] - 1, g.L.n[2] - 1};
-  Shell sh = make_shell(g.L, zero, top);
+  // grid nodes, extended by one ghost layer behind faces inside a larger grid
+  int a[3], b[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = g.L.bc[2 * d] == BC_EXCHANGE ? -1 : 0;
+    b[d] = g.L.bc[2 * d + 1] == BC_EXCHANGE ? g.L.n[d] : g.L.n[d] - 1;
+  }
+  const long long N = (long long)(b[0] - a[0] + 1) * (b[1] - a[1] + 1) * (b[2] - a[2] + 1);
+  Shell sh = make_shell(g.L, a, b);  // the remaining ghost nodes copy the node their index maps to
   if (g.prec == JZ_P32) {
-    k_metrics<float><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (float*)g.M);
+    k_metrics<float><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (float*)g.M, a[0], a[1], a[2], b[0], b[1], b[2]);
     k_fill_ghosts<float><<<grid_blocks(sh.total(), 256), 256, 0, s>>>(g.L, sh, (float*)g.M, 10);
   } else {
-    k_metrics<double><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (double*)g.M);
+    k_metrics<double><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (double*)g.M, a[0], a[1], a[2], b[0], b[1], b[2]);
     k_fill_ghosts<double><<<grid_blocks(sh.total(), 256), 256, 0, s>>>(g.L, sh, (double*)g.M, 10);
   }
   count_launches(2);
@@ -474,9 +523,11 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
   k_inflow<<<grid_blocks((long long)g.L.n[1] * g.L.n[2], 256), 256, 0, s>>>(g.L, g.C, g.F, g.inflow);
   count_launches(1);
   if (g.prec == JZ_P64)
-    k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0);
+    k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0, g.goff[0], g.goff[1],
+                                                       g.goff[2], g.gn[0], g.gn[1]);
   else
-    k_init<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (float*)g.Q0);
+    k_init<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (float*)g.Q0, g.goff[0], g.goff[1],
+                                                      g.goff[2], g.gn[0], g.gn[1]);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -560,6 +611,19 @@ cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s) {
     k_pack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.Q0, dense);
   else
     k_pack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.Q0, dense);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(int prec, const void* entries, int begin, int count, int blocks, int which,
+                            cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const XEntry* X = (const XEntry*)entries + begin;
+  const dim3 grid(blocks, count);
+  if (prec == JZ_P64)
+    k_exchange<double><<<grid, 256, 0, s>>>(X, which);
+  else
+    k_exchange<float><<<grid, 256, 0, s>>>(X, which);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ struct GridDev {
   double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
+  int goff[3], gn[3];  // global index of local node 0 and global node counts (blocks; else 0 and n)
   int variant;         // stage kernel of P32: 0 scalar, 1 paired FP32x2, 2 vector records
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
@@ -41,6 +42,7 @@ Shell make_shell(const Layout& L, const int a[3], const int b[3]);
 
 struct TabParams {
   int n[3], per[3];
+  int off[3], gn[3];  // global index of local node 0, global node counts (a block of a larger grid)
   double lo[3], hi[3];
   double cluster_r, stretch_c, stretch_w, amp;
   int m[9];
@@ -63,12 +65,26 @@ size_t bc_ctx_bytes();
 void bc_ctx_fill(void* host_dst, const GridDev& g, int* blocks);
 cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, cudaStream_t s);
 
+// halo exchange between blocks of one grid: one entry per (block, exchange face)
+struct XEntry {
+  void* dq[3];                       // Q0, QA, QB of the block whose ghosts are filled
+  void* sq[3];                       // Q0, QA, QB of the neighbouring block
+  long long dpitch, dplane, dnpad;   // strides (elements) of the two layouts
+  long long spitch, splane, snpad;
+  int d;                             // direction of the face normal
+  int dfirst, sfirst;                // first local index along d of the ghost layers / the copied layers
+  int ea, eb;                        // padded node counts of the other two directions (i, j, k order)
+};
+cudaError_t launch_exchange(int prec, const void* entries, int begin, int count, int blocks, int which,
+                            cudaStream_t s);
+
 // jz_reduce.cu
 cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s);
 cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s);
 size_t rate_ctx_bytes();
 void rate_ctx_fill(void* host_dst, const GridDev& g);
-cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, cudaStream_t s);
+// coupled: the grids are blocks of one grid and share its time step
+cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, bool coupled, cudaStream_t s);
 
 // jz_stage.cu
 struct StageTiling { int ti, tj; };

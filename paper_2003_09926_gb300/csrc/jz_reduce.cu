@@ -43,7 +43,8 @@ __device__ bool last_block(unsigned int* counter) {
 
 template <typename ST, typename MT>
 __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, const ST* __restrict__ Q,
-                                              const MT* __restrict__ M, Scalars* sc, double* partial, double cfl) {
+                                              const MT* __restrict__ M, Scalars* sc, double* partial, double cfl,
+                                              bool finalize = true) {
   const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
   const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
   const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
@@ -113,10 +114,14 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
     if (threadIdx.x == 0) {
       for (int w = 1; w < RED_THREADS / 32; ++w) m = fmax(m, red[w]);
       m = fmax(m, red[0]);
-      double dt = cfl / m;
-      sc->dt = dt;
-      sc->time += dt;
-      sc->step += 1;
+      if (finalize) {
+        double dt = cfl / m;
+        sc->dt = dt;
+        sc->time += dt;
+        sc->step += 1;
+      } else {
+        sc->rate = m;  // the blocks' rates are combined by k_rate_combine
+      }
       sc->count = 0;
     }
   }
@@ -140,9 +145,25 @@ struct RateCtx {
 };
 
 template <typename ST, typename MT>
-__global__ void __launch_bounds__(RED_THREADS) k_timestep_batch(const RateCtx* __restrict__ ctx, double cfl) {
+__global__ void __launch_bounds__(RED_THREADS) k_timestep_batch(const RateCtx* __restrict__ ctx, double cfl,
+                                                                bool finalize) {
   const RateCtx& X = ctx[blockIdx.y];
-  timestep_body<ST, MT>(X.L, X.F, (const ST*)X.Q0, (const MT*)X.M, X.sc, X.partial, cfl);
+  timestep_body<ST, MT>(X.L, X.F, (const ST*)X.Q0, (const MT*)X.M, X.sc, X.partial, cfl, finalize);
+}
+
+// Blocks of one grid: the grid's rate is the largest of its blocks' (exact
+// in any order), and every block takes the one time step it gives.
+__global__ void k_rate_combine(const RateCtx* __restrict__ ctx, int n, double cfl) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double m = 0.0;
+  for (int b = 0; b < n; ++b) m = fmax(m, ctx[b].sc->rate);
+  const double dt = cfl / m;
+  for (int b = 0; b < n; ++b) {
+    Scalars* sc = ctx[b].sc;
+    sc->dt = dt;
+    sc->time += dt;
+    sc->step += 1;
+  }
 }
 
 __global__ void k_fixed_dt(Scalars* sc, double dt) {
@@ -297,15 +318,20 @@ void rate_ctx_fill(void* dst, const GridDev& g) {
   X.partial = g.partial;
 }
 
-cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, cudaStream_t s) {
+cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, bool coupled, cudaStream_t s) {
   const dim3 grid(64, n);  // 64 blocks per grid (partials hold RED_BLOCKS)
   const RateCtx* X = (const RateCtx*)ctx;
+  const bool fin = !coupled;
   switch (prec) {
-    case JZ_P64: k_timestep_batch<double, double><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
-    case JZ_P32_M64: k_timestep_batch<float, double><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
-    default: k_timestep_batch<float, float><<<grid, RED_THREADS, 0, s>>>(X, cfl); break;
+    case JZ_P64: k_timestep_batch<double, double><<<grid, RED_THREADS, 0, s>>>(X, cfl, fin); break;
+    case JZ_P32_M64: k_timestep_batch<float, double><<<grid, RED_THREADS, 0, s>>>(X, cfl, fin); break;
+    default: k_timestep_batch<float, float><<<grid, RED_THREADS, 0, s>>>(X, cfl, fin); break;
   }
   count_launches(1);
+  if (coupled) {
+    k_rate_combine<<<1, 32, 0, s>>>(X, n, cfl);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 

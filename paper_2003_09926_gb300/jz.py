@@ -74,6 +74,12 @@ def lib() -> C.CDLL:
             "jz_batch_create": ([C.POINTER(G), C.c_int, VP, C.c_size_t, VP, C.POINTER(B)], C.c_int),
             "jz_batch_nsteps": ([B, C.c_int, C.c_double], C.c_int),
             "jz_batch_destroy": ([B], C.c_int),
+            "jz_block_bytes": ([C.POINTER(GridDesc), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
+                               C.c_int),
+            "jz_block_create": ([C.POINTER(GridDesc), C.POINTER(C.c_int), C.POINTER(C.c_int), VP, C.c_size_t, VP,
+                                 C.POINTER(G)], C.c_int),
+            "jz_blocks_bytes": ([C.POINTER(G), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+            "jz_blocks_create": ([C.POINTER(G), C.c_int, VP, C.c_size_t, VP, C.POINTER(B)], C.c_int),
             "jz_launch_count": ([C.POINTER(C.c_uint64)], C.c_int),
             "jz_profile_begin": ([G], C.c_int),
             "jz_profile_read": ([G, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
@@ -145,6 +151,21 @@ def jz_grid_bytes(desc: dict) -> int:
 def jz_grid_create(desc: dict, dev_ptr: int, nbytes: int, stream: int) -> C.c_void_p:
     h = C.c_void_p()
     _check(lib().jz_grid_create(C.byref(make_desc(desc)), C.c_void_p(dev_ptr), nbytes, C.c_void_p(stream), C.byref(h)))
+    return h
+
+
+def jz_block_bytes(desc: dict, o0, o1) -> int:
+    out = C.c_size_t(0)
+    a, b = (C.c_int * 3)(*o0), (C.c_int * 3)(*o1)
+    _check(lib().jz_block_bytes(C.byref(make_desc(desc)), a, b, C.byref(out)))
+    return out.value
+
+
+def jz_block_create(desc: dict, o0, o1, dev_ptr: int, nbytes: int, stream: int) -> C.c_void_p:
+    h = C.c_void_p()
+    a, b = (C.c_int * 3)(*o0), (C.c_int * 3)(*o1)
+    _check(lib().jz_block_create(C.byref(make_desc(desc)), a, b, C.c_void_p(dev_ptr), nbytes, C.c_void_p(stream),
+                                 C.byref(h)))
     return h
 
 
@@ -243,19 +264,29 @@ def _torch():
 
 
 class Grid:
-    """A grid living in a torch-allocated device buffer on a CUDA stream."""
+    """A grid living in a torch-allocated device buffer on a CUDA stream;
+    with ``block=(o0, o1)`` the block of nodes [o0, o1] (i, j, k order,
+    inclusive) of the grid ``desc`` describes."""
 
-    def __init__(self, desc: dict, stream=None, device: int = 0):
+    def __init__(self, desc: dict, stream=None, device: int = 0, block=None):
         torch = _torch()
         self.desc = dict(desc)
         self.device = device
-        self.nbytes = jz_grid_bytes(desc)
+        self.block = None if block is None else (tuple(block[0]), tuple(block[1]))
+        if self.block is None:
+            self.nbytes = jz_grid_bytes(desc)
+            ni, nj, nk = desc["ni"], desc["nj"], desc["nk"]
+        else:
+            self.nbytes = jz_block_bytes(desc, *self.block)
+            ni, nj, nk = (self.block[1][a] - self.block[0][a] + 1 for a in range(3))
         self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
         ptr = self.buf.data_ptr()
         self.ptr = (ptr + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
-        self.h = jz_grid_create(desc, self.ptr, self.nbytes, self.stream.cuda_stream)
-        ni, nj, nk = desc["ni"], desc["nj"], desc["nk"]
+        if self.block is None:
+            self.h = jz_grid_create(desc, self.ptr, self.nbytes, self.stream.cuda_stream)
+        else:
+            self.h = jz_block_create(desc, *self.block, self.ptr, self.nbytes, self.stream.cuda_stream)
         self.shape = (5, nk, nj, ni)
 
     def init(self, flow: dict, seed: int):
@@ -298,19 +329,24 @@ class Grid:
 
 
 class Batch:
-    def __init__(self, grids: list[Grid], stream=None):
+    """Independent grids stepped together; with ``coupled=True`` the blocks
+    of one grid (halo exchange and one shared time step)."""
+
+    def __init__(self, grids: list[Grid], stream=None, coupled: bool = False):
         torch = _torch()
         self.grids = grids
         arr = (C.c_void_p * len(grids))(*[g.h.value for g in grids])
         self._arr = arr
         nb = C.c_size_t(0)
-        _check(lib().jz_batch_bytes(arr, len(grids), C.byref(nb)))
+        size_fn, create_fn = ((lib().jz_blocks_bytes, lib().jz_blocks_create) if coupled
+                              else (lib().jz_batch_bytes, lib().jz_batch_create))
+        _check(size_fn(arr, len(grids), C.byref(nb)))
         self.buf = torch.empty(nb.value + 256, dtype=torch.uint8, device=grids[0].buf.device)
         ptr = (self.buf.data_ptr() + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.Stream(device=grids[0].device)
         self.h = C.c_void_p()
-        _check(lib().jz_batch_create(arr, len(grids), C.c_void_p(ptr), nb.value, C.c_void_p(self.stream.cuda_stream),
-                                     C.byref(self.h)))
+        _check(create_fn(arr, len(grids), C.c_void_p(ptr), nb.value, C.c_void_p(self.stream.cuda_stream),
+                         C.byref(self.h)))
 
     def nsteps(self, n: int, cfl: float):
         _check(lib().jz_batch_nsteps(self.h, n, cfl))
