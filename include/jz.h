@@ -209,6 +209,43 @@ int jz_batch_destroy(jz_batch* b);
 int jz_blocks_bytes(jz_grid* const* blocks, int n, size_t* bytes);
 int jz_blocks_create(jz_grid* const* blocks, int n, void* dev_buf, size_t bytes, void* stream, jz_batch** out);
 
+/* --- time statistics and restart (Section 6) --------------------------------
+ * The paper's validation averages the solution in time once the jet is
+ * statistically steady: the time-averaged axial velocity <U>, the rms of its
+ * fluctuation u_rms, radial profiles of both at fixed distances downstream of
+ * the inlet (averaged in the azimuthal direction), and the potential core,
+ * where <U> is at least 95% of the jet's inlet velocity.
+ *
+ * jz_stats_bytes / jz_stats_create: running FP64 sums of u = (rho u)/rho and
+ *   u^2 over samples for every node of grid g, in a caller-owned device
+ *   buffer (256-byte aligned); created zeroed on the grid's stream.
+ * jz_stats_sample: adds the grid's current state (enqueued on its stream; in
+ *   sample order, so the sums are those of a sequential loop).
+ * jz_stats_read: per node ([k][j][i], the grid's nodes), <U> = sum / N and
+ *   u_rms = sqrt(max(sum2 / N - <U>^2, 0)); n must be the node count.
+ * jz_stats_radial: the i-plane whose axial coordinate (at the node nearest the
+ *   axis) is nearest x; its nodes binned by r = sqrt(y^2 + z^2) into nbins
+ *   equal bins of [0, r_max): per bin the mean of <U>, the mean of u_rms and
+ *   the node count (empty bins 0).
+ * jz_stats_core_length: <U> on the axis (the mean over the node lines nearest
+ *   y = z = 0: the middle line of an odd node count, both middle lines of an
+ *   even one) and the axial distance from the inlet to its first drop below
+ *   frac * u_jet, interpolated linearly (the last node's x if it never drops).
+ * The read functions synchronise the grid's stream; JZ_EINVAL without samples
+ * or for bad arguments.
+ * jz_set_clock sets the grid's simulated time and step count (restarting from
+ * a saved state: jz_state_upload, then jz_set_clock). */
+typedef struct jz_stats jz_stats;
+int jz_stats_bytes(jz_grid* g, size_t* bytes);
+int jz_stats_create(jz_grid* g, void* dev_buf, size_t bytes, jz_stats** out);
+int jz_stats_sample(jz_stats* s);
+int jz_stats_count(jz_stats* s, int64_t* samples);
+int jz_stats_read(jz_stats* s, double* mean_u, double* rms_u, size_t n);
+int jz_stats_radial(jz_stats* s, double x, int nbins, double r_max, double* mean_u, double* rms_u, double* count);
+int jz_stats_core_length(jz_stats* s, double u_jet, double frac, double* length);
+int jz_stats_destroy(jz_stats* s);
+int jz_set_clock(jz_grid* g, double time, int64_t step);
+
 /* --- measurement helpers -------------------------------------------------- */
 
 /* Number of kernel launches this library has issued in this process

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_stage_pair.cu", "jz_stage_v.cu", "jz_static.cu", "jz_peak.cu"]
+SOURCES = ["jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_stage_pair.cu", "jz_stage_v.cu", "jz_static.cu", "jz_peak.cu", "jz_stats.cu"]
 
 
 def nvcc() -> str:
@@ -41,7 +41,10 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
     if not _deps_newer(obj, path):
         return obj
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", path, "-o", obj + ".tmp"]
+    # host code: no fused multiply-add contraction (results that the host
+    # forms, such as the statistics' rms, then round as plainly written)
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+           "-c", path, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -918,4 +918,200 @@ int jz_batch_destroy(jz_batch* b) {
   return JZ_OK;
 }
 
+// ---- time statistics -------------------------------------------------------
+
+int jz_set_clock(jz_grid* g, double time, int64_t step) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!std::isfinite(time) || step < 0) return fail(JZ_EINVAL, "bad clock (time %g, step %lld)", time, (long long)step);
+  Scalars* sc = g->dev.sc;
+  JZ_CUDA(cudaMemcpyAsync(&sc->time, &time, sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  long long st = step;
+  JZ_CUDA(cudaMemcpyAsync(&sc->step, &st, sizeof(long long), cudaMemcpyHostToDevice, g->stream));
+  JZ_CUDA(cudaStreamSynchronize(g->stream));  // the host values go out of scope
+  return JZ_OK;
+}
+
+}  // extern "C"
+
+struct jz_stats {
+  jz_grid* g = nullptr;
+  double* su = nullptr;   // sum of u over samples, per node [k][j][i]
+  double* su2 = nullptr;  // sum of u^2
+  double* scr = nullptr;  // plane coordinates / axial coordinates
+  int64_t samples = 0;
+};
+
+namespace {
+
+struct StatsCarve { size_t off_su, off_su2, off_scr, total; };
+
+StatsCarve stats_carve(const jz_grid* g) {
+  const Layout& L = g->dev.L;
+  const size_t N = (size_t)L.n[0] * L.n[1] * L.n[2];
+  const size_t scr = std::max((size_t)2 * L.n[1] * L.n[2], (size_t)L.n[0]);
+  StatsCarve c;
+  size_t off = 0;
+  c.off_su = off; off = align256(off + 8 * N);
+  c.off_su2 = off; off = align256(off + 8 * N);
+  c.off_scr = off; off = align256(off + 8 * scr);
+  c.total = off;
+  return c;
+}
+
+// plane index of the grid nodes nearest the axis along j or k: both
+// middle nodes of an even count, the middle node of an odd one
+void axis_nodes(int n, int c[2], int& m) {
+  if (n % 2 == 0) { c[0] = n / 2 - 1; c[1] = n / 2; m = 2; }
+  else { c[0] = c[1] = n / 2; m = 1; }
+}
+
+}  // namespace
+
+extern "C" {
+
+int jz_stats_bytes(jz_grid* g, size_t* bytes) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!bytes) return fail(JZ_EINVAL, "null output");
+  *bytes = stats_carve(g).total;
+  return JZ_OK;
+}
+
+int jz_stats_create(jz_grid* g, void* dev_buf, size_t bytes, jz_stats** out) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!out) return fail(JZ_EINVAL, "null output");
+  *out = nullptr;
+  const StatsCarve c = stats_carve(g);
+  if (!dev_buf || ((uintptr_t)dev_buf & 255)) return fail(JZ_EINVAL, "statistics buffer must be non-null and 256-byte aligned");
+  if (bytes < c.total) return fail(JZ_ENOMEM, "statistics buffer holds %zu bytes, needs %zu", bytes, c.total);
+  jz_stats* s = new (std::nothrow) jz_stats();
+  if (!s) return fail(JZ_ENOMEM, "host allocation failed");
+  s->g = g;
+  s->su = (double*)((char*)dev_buf + c.off_su);
+  s->su2 = (double*)((char*)dev_buf + c.off_su2);
+  s->scr = (double*)((char*)dev_buf + c.off_scr);
+  if (cudaMemsetAsync(dev_buf, 0, c.off_scr, g->stream) != cudaSuccess) {
+    delete s;
+    return fail(JZ_ECUDA, "clearing the statistics failed");
+  }
+  *out = s;
+  return JZ_OK;
+}
+
+int jz_stats_sample(jz_stats* s) {
+  if (!s) return fail(JZ_EINVAL, "null statistics");
+  JZ_CUDA(launch_stats_sample(s->g->dev, s->su, s->su2, s->g->stream));
+  ++s->samples;
+  return JZ_OK;
+}
+
+int jz_stats_count(jz_stats* s, int64_t* samples) {
+  if (!s || !samples) return fail(JZ_EINVAL, "null argument");
+  *samples = s->samples;
+  return JZ_OK;
+}
+
+int jz_stats_read(jz_stats* s, double* mean_u, double* rms_u, size_t n) {
+  if (!s || !mean_u || !rms_u) return fail(JZ_EINVAL, "null argument");
+  const Layout& L = s->g->dev.L;
+  const size_t N = (size_t)L.n[0] * L.n[1] * L.n[2];
+  if (n != N) return fail(JZ_EINVAL, "host arrays hold %zu values, the grid has %zu nodes", n, N);
+  if (s->samples < 1) return fail(JZ_EINVAL, "no samples");
+  JZ_CUDA(cudaMemcpyAsync(mean_u, s->su, 8 * N, cudaMemcpyDeviceToHost, s->g->stream));
+  JZ_CUDA(cudaMemcpyAsync(rms_u, s->su2, 8 * N, cudaMemcpyDeviceToHost, s->g->stream));
+  JZ_CUDA(cudaStreamSynchronize(s->g->stream));
+  const double ns = (double)s->samples;
+  for (size_t t = 0; t < N; ++t) {
+    const double m = mean_u[t] / ns;
+    mean_u[t] = m;
+    rms_u[t] = std::sqrt(std::max(rms_u[t] / ns - m * m, 0.0));
+  }
+  return JZ_OK;
+}
+
+int jz_stats_radial(jz_stats* s, double x, int nbins, double r_max, double* mean_u, double* rms_u, double* count) {
+  if (!s || !mean_u || !rms_u || !count) return fail(JZ_EINVAL, "null argument");
+  if (nbins < 1 || !(r_max > 0.0)) return fail(JZ_EINVAL, "need nbins >= 1 and r_max > 0");
+  if (s->samples < 1) return fail(JZ_EINVAL, "no samples");
+  const Layout& L = s->g->dev.L;
+  const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+  cudaStream_t st = s->g->stream;
+  // the plane whose axial coordinate (at the node nearest the axis) is nearest x
+  int cj[2], ck[2], mj, mk;
+  axis_nodes(n1, cj, mj);
+  axis_nodes(n2, ck, mk);
+  std::vector<double> xs(n0);
+  JZ_CUDA(launch_stats_axis_x(s->g->dev, cj[0], ck[0], s->scr, st));
+  JZ_CUDA(cudaMemcpyAsync(xs.data(), s->scr, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
+  JZ_CUDA(cudaStreamSynchronize(st));
+  int ip = 0;
+  for (int i = 1; i < n0; ++i)
+    if (std::fabs(xs[i] - x) < std::fabs(xs[ip] - x)) ip = i;
+  const size_t m = (size_t)n1 * n2;
+  std::vector<double> yz(2 * m), su(m), su2(m);
+  JZ_CUDA(launch_stats_plane_yz(s->g->dev, ip, s->scr, st));
+  JZ_CUDA(cudaMemcpyAsync(yz.data(), s->scr, 16 * m, cudaMemcpyDeviceToHost, st));
+  JZ_CUDA(cudaMemcpy2DAsync(su.data(), 8, s->su + ip, 8 * (size_t)n0, 8, m, cudaMemcpyDeviceToHost, st));
+  JZ_CUDA(cudaMemcpy2DAsync(su2.data(), 8, s->su2 + ip, 8 * (size_t)n0, 8, m, cudaMemcpyDeviceToHost, st));
+  JZ_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < nbins; ++b) mean_u[b] = rms_u[b] = count[b] = 0.0;
+  const double ns = (double)s->samples;
+  for (size_t t = 0; t < m; ++t) {  // nodes in [k][j] order
+    const double r = std::sqrt(yz[2 * t] * yz[2 * t] + yz[2 * t + 1] * yz[2 * t + 1]);
+    if (!(r < r_max)) continue;
+    const int b = std::min(nbins - 1, (int)(r / r_max * nbins));
+    const double mu = su[t] / ns;
+    mean_u[b] += mu;
+    rms_u[b] += std::sqrt(std::max(su2[t] / ns - mu * mu, 0.0));
+    count[b] += 1.0;
+  }
+  for (int b = 0; b < nbins; ++b)
+    if (count[b] > 0.0) {
+      mean_u[b] /= count[b];
+      rms_u[b] /= count[b];
+    }
+  return JZ_OK;
+}
+
+int jz_stats_core_length(jz_stats* s, double u_jet, double frac, double* length) {
+  if (!s || !length) return fail(JZ_EINVAL, "null argument");
+  if (!(u_jet > 0.0) || !(frac > 0.0)) return fail(JZ_EINVAL, "need u_jet > 0 and frac > 0");
+  if (s->samples < 1) return fail(JZ_EINVAL, "no samples");
+  const Layout& L = s->g->dev.L;
+  const int n0 = L.n[0], n1 = L.n[1];
+  cudaStream_t st = s->g->stream;
+  int cj[2], ck[2], mj, mk;
+  axis_nodes(L.n[1], cj, mj);
+  axis_nodes(L.n[2], ck, mk);
+  std::vector<double> xs(n0), axis(n0, 0.0), line(n0);
+  JZ_CUDA(launch_stats_axis_x(s->g->dev, cj[0], ck[0], s->scr, st));
+  JZ_CUDA(cudaMemcpyAsync(xs.data(), s->scr, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
+  JZ_CUDA(cudaStreamSynchronize(st));
+  // <U> on the axis: the mean over the one, two or four node lines around it
+  for (int a = 0; a < mj; ++a)
+    for (int b = 0; b < mk; ++b) {
+      const size_t off = (size_t)n0 * (cj[a] + (size_t)n1 * ck[b]);
+      JZ_CUDA(cudaMemcpyAsync(line.data(), s->su + off, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
+      JZ_CUDA(cudaStreamSynchronize(st));
+      for (int i = 0; i < n0; ++i) axis[i] += line[i];
+    }
+  const double level = frac * u_jet, ns = (double)s->samples * mj * mk;
+  for (int i = 0; i < n0; ++i) axis[i] /= ns;
+  // the first crossing below frac * u_jet from the inlet, interpolated linearly
+  double len = xs[n0 - 1];
+  if (axis[0] < level) len = xs[0];
+  else
+    for (int i = 1; i < n0; ++i)
+      if (axis[i] < level) {
+        len = xs[i - 1] + (xs[i] - xs[i - 1]) * (axis[i - 1] - level) / (axis[i - 1] - axis[i]);
+        break;
+      }
+  *length = len;
+  return JZ_OK;
+}
+
+int jz_stats_destroy(jz_stats* s) {
+  delete s;
+  return JZ_OK;
+}
+
 }  // extern "C"

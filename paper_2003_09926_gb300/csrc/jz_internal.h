@@ -78,6 +78,11 @@ struct XEntry {
 cudaError_t launch_exchange(int prec, const void* entries, int begin, int count, int blocks, int which,
                             cudaStream_t s);
 
+// jz_stats.cu: time statistics of the axial velocity
+cudaError_t launch_stats_sample(const GridDev& g, double* su, double* su2, cudaStream_t s);
+cudaError_t launch_stats_plane_yz(const GridDev& g, int i, double* yz, cudaStream_t s);
+cudaError_t launch_stats_axis_x(const GridDev& g, int jc, int kc, double* x, cudaStream_t s);
+
 // jz_reduce.cu
 cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s);
 cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s);

@@ -79,6 +79,16 @@ def lib() -> C.CDLL:
             "jz_block_create": ([C.POINTER(GridDesc), C.POINTER(C.c_int), C.POINTER(C.c_int), VP, C.c_size_t, VP,
                                  C.POINTER(G)], C.c_int),
             "jz_blocks_bytes": ([C.POINTER(G), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+            "jz_stats_bytes": ([G, C.POINTER(C.c_size_t)], C.c_int),
+            "jz_stats_create": ([G, VP, C.c_size_t, C.POINTER(VP)], C.c_int),
+            "jz_stats_sample": ([VP], C.c_int),
+            "jz_stats_count": ([VP, C.POINTER(C.c_int64)], C.c_int),
+            "jz_stats_read": ([VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "jz_stats_radial": ([VP, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+            "jz_stats_core_length": ([VP, C.c_double, C.c_double, C.POINTER(C.c_double)], C.c_int),
+            "jz_stats_destroy": ([VP], C.c_int),
+            "jz_set_clock": ([G, C.c_double, C.c_int64], C.c_int),
             "jz_blocks_create": ([C.POINTER(G), C.c_int, VP, C.c_size_t, VP, C.POINTER(B)], C.c_int),
             "jz_launch_count": ([C.POINTER(C.c_uint64)], C.c_int),
             "jz_profile_begin": ([G], C.c_int),
@@ -315,6 +325,18 @@ class Grid:
     def synchronize(self):
         self.stream.synchronize()
 
+    def save(self, path: str):
+        """Restart file: the state of the grid's nodes (FP64) and its clock."""
+        d = self.diagnostics(allow_nonfinite=True)
+        np.savez(path, Q=self.download(), time=d["time"], step=d["step"], dt=d["dt"])
+
+    def load(self, path: str):
+        """Restart from a file written by save (the flow parameters are set by init)."""
+        with np.load(path) as z:
+            self.upload(z["Q"])
+            _check(lib().jz_set_clock(self.h, float(z["time"]), int(z["step"])))
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             jz_grid_destroy(self.h)
@@ -354,5 +376,54 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().jz_batch_destroy(self.h)
+            self.h = None
+        self.buf = None
+
+
+class Stats:
+    """Time statistics of a grid's axial velocity (running sums on the device)."""
+
+    def __init__(self, grid: Grid):
+        torch = _torch()
+        self.grid = grid
+        nb = C.c_size_t(0)
+        _check(lib().jz_stats_bytes(grid.h, C.byref(nb)))
+        self.buf = torch.empty(nb.value + 256, dtype=torch.uint8, device=grid.buf.device)
+        ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.h = C.c_void_p()
+        _check(lib().jz_stats_create(grid.h, C.c_void_p(ptr), nb.value, C.byref(self.h)))
+
+    def sample(self):
+        _check(lib().jz_stats_sample(self.h))
+
+    @property
+    def samples(self) -> int:
+        n = C.c_int64(0)
+        _check(lib().jz_stats_count(self.h, C.byref(n)))
+        return n.value
+
+    def read(self):
+        """(<U>, u_rms) per node, arrays of shape (nk, nj, ni)."""
+        shape = self.grid.shape[1:]
+        m, r = np.empty(shape), np.empty(shape)
+        _check(lib().jz_stats_read(self.h, m.ctypes.data_as(C.POINTER(C.c_double)),
+                                   r.ctypes.data_as(C.POINTER(C.c_double)), m.size))
+        return m, r
+
+    def radial(self, x: float, nbins: int, r_max: float):
+        """(mean <U>, mean u_rms, node count) per radial bin at the plane nearest x."""
+        m, r, c = np.empty(nbins), np.empty(nbins), np.empty(nbins)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(lib().jz_stats_radial(self.h, x, nbins, r_max, dp(m), dp(r), dp(c)))
+        return m, r, c
+
+    def core_length(self, u_jet: float, frac: float = 0.95) -> float:
+        out = C.c_double(0.0)
+        _check(lib().jz_stats_core_length(self.h, u_jet, frac, C.byref(out)))
+        return out.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jz_stats_destroy(self.h)
             self.h = None
         self.buf = None
