@@ -64,6 +64,16 @@ extern "C" {
 #define JZ_IC_JET 0       /* top-hat jet column plus seeded velocity noise     */
 #define JZ_IC_QUIESCENT 1 /* air at rest (Section 5.1: the paper's start state) */
 
+/* Subgrid-scale eddy viscosity mu_t (Section 3 names an LES formulation,
+ * not a model), Delta = J^(-1/3):
+ *   JZ_SGS_SMAGORINSKY: mu_t = rho (C_s Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij);
+ *   JZ_SGS_VREMAN:      mu_t = rho c sqrt(B_b / (a_ij a_ij)), c = 2.5 C_s^2,
+ *     a_ij = du_j/dx_i, b_ij = Delta^2 a_mi a_mj, B_b = b11 b22 - b12^2
+ *     + b11 b33 - b13^2 + b22 b33 - b23^2 (0 where a = 0; Vreman's model,
+ *     which vanishes in pure shear). */
+#define JZ_SGS_SMAGORINSKY 0
+#define JZ_SGS_VREMAN 1
+
 /* Grid descriptor.  Nodes are numbered 0..n-1 per direction (i fastest);
  * non-periodic directions need n >= 3 and their first and last nodes are
  * boundary nodes set by the boundary conditions.  Coordinates: x is uniform
@@ -82,13 +92,14 @@ typedef struct jz_grid_desc {
 } jz_grid_desc;
 
 /* Flow parameters.  re <= 0 means inviscid (no molecular viscosity);
- * cs = 0 disables the Smagorinsky eddy viscosity; k2, k4, sigma are the
+ * cs = 0 disables the eddy viscosity; k2, k4, sigma are the
  * dissipation constants; s1 is the Sutherland constant over T_inf; r0 and
  * theta shape the jet profile u = (M/2)(1 - tanh((r - r0)/(2 theta))); noise
  * is the velocity-noise amplitude relative to the jet velocity. */
 typedef struct jz_flow_params {
   double mach, re, gamma, pr, prt, cs, k2, k4, sigma, s1, r0, theta, noise;
-  int ic; /* JZ_IC_JET or JZ_IC_QUIESCENT */
+  int ic;  /* JZ_IC_JET or JZ_IC_QUIESCENT */
+  int sgs; /* JZ_SGS_SMAGORINSKY or JZ_SGS_VREMAN (cs = 0: no eddy viscosity) */
 } jz_flow_params;
 
 /* Diagnostics over all grid nodes (ghosts excluded), reduced in a fixed
@@ -278,14 +289,12 @@ int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
 int jz_set_tiling(jz_grid* g, int kc);
 
 /* Stage kernel variant of a JZ_P32 grid: 2 (default) keeps node records as
- * float4 + float vectors in shared memory (three block barriers per plane);
+ * float4 + float vectors in shared memory (two block barriers per plane);
  * 0 is the scalar kernel (one shared-memory value per load, four barriers
- * per plane); 1 pairs two nodes per thread and computes them with packed
- * FP32x2 instructions (fewer instructions, but half the resident warps).
- * All three evaluate the same formulas; results agree to FP32 rounding.
- * Measured on the 256x192x192 mapped jet (ms per stage): 2: 0.44,
- * 0: 0.55, 1: 0.61.  JZ_EINVAL for other precisions or variants.  A batch
- * uses its first grid's variant. */
+ * per plane).  Both evaluate the same formulas; results agree to FP32
+ * rounding.  Measured on the 256x192x192 mapped jet: 0.41 ms (2) and 0.55 ms
+ * (0) per stage.  JZ_EINVAL for other precisions or variants.  A batch uses
+ * its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
 /* --- diagnostics without device allocation --------------------------------

@@ -53,14 +53,14 @@ class _Grid(C.Structure):
         ("bc", C.c_int * 6),
         ("lo", C.c_double * 3), ("hi", C.c_double * 3),
         ("cluster_r", C.c_double), ("stretch_c", C.c_double), ("stretch_w", C.c_double),
-        ("map_amp", C.c_double), ("map_seed", C.c_uint64),
+        ("map_amp", C.c_double), ("map_seed", C.c_uint64), ("geom", C.c_int),
     ]
 
 
 class _Flow(C.Structure):
     _fields_ = [(n, C.c_double) for n in
                 ("mach", "re", "gamma", "pr", "prt", "cs", "k2", "k4", "sigma", "s1", "r0", "theta", "noise")] + [
-        ("ic", C.c_int)]
+        ("ic", C.c_int), ("sgs", C.c_int)]
 
 
 def lib():
@@ -110,13 +110,14 @@ def make_grid(desc: dict) -> _Grid:
     g.stretch_w = desc.get("stretch_w", 0.5)
     g.map_amp = desc.get("map_amp", 0.0)
     g.map_seed = desc.get("map_seed", 0)
+    g.geom = desc.get("geom", 0)
     return g
 
 
 def make_flow(flow: dict) -> _Flow:
     f = _Flow()
     for n, _ in _Flow._fields_:
-        setattr(f, n, flow[n])
+        setattr(f, n, flow.get(n, 0) if n == "sgs" else flow[n])
     return f
 
 

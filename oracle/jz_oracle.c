@@ -29,9 +29,26 @@
  *       ghost layers copy (zeroth order) or wrap (periodic).
  *   R9  Turkel-Vatsa constants k2 = 1/4, k4 = 1/256, sigma = 1/2, sensor
  *       maximum taken over the two nodes of a face.
- *   R10 SGS model: Smagorinsky, Delta = J^{-1/3}, C_s = 0.18, Pr_t = 0.9.
+ *   R10 SGS model: Smagorinsky, Delta = J^{-1/3}, C_s = 0.18, Pr_t = 0.9;
+ *       optionally Vreman's model with c = 2.5 C_s^2 and the same Delta.
  *   R11 Jameson 5-stage coefficients alpha = (1/4, 1/6, 3/8, 1/2, 1).
  *   R12 time step from a CFL number and the convective + viscous spectral radii.
+ *   R14 cylindrical grid (Section 3): xi axial, eta radial from the centreline
+ *       r = 0, zeta azimuthal with nk points whose first and last coincide
+ *       (period P = nk - 1, P even).  Centreline nodes: the conserved
+ *       variables of the adjacent radial node line (eta = 1) averaged over the
+ *       P distinct azimuthal nodes, summed in azimuthal order (zeroth-order
+ *       extrapolation, then the average); ghost nodes behind the centreline
+ *       are the nodes across it, (xi, -eta, zeta + P/2); the last azimuthal
+ *       plane is a copy of the first.
+ *   R15 the conservative metric form gives zero volume (1/J = 0) on the
+ *       centreline; J there is taken from the node at eta = 1.  The
+ *       centreline's eta-flux enters its neighbours through S^eta, which
+ *       vanishes there, so J only affects the time-step bound and the
+ *       diagnostics' volume weights.  A far-field node on the centreline
+ *       takes its outward normal from the node at eta = 1.  Where a
+ *       directional spectral radius
+ *       is zero its anisotropic scaling is zero (the limit for sigma < 1).
  *
  * Array layout (private to the oracle): every field is a dense array over the
  * padded box (ni+4) x (nj+4) x (nk+4) (two ghost layers on every face),
@@ -49,7 +66,8 @@
 #define NG 2
 #define PI 3.14159265358979323846
 
-enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2 };
+enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2, BC_AXIS = 4 };
+enum { GEOM_BOX = 0, GEOM_CYLINDER = 1 };
 enum { IC_JET = 0, IC_QUIESCENT = 1 };
 
 typedef struct {
@@ -61,11 +79,13 @@ typedef struct {
   double stretch_w;     /* R4: clustering width w */
   double map_amp;       /* R5: offset amplitude in units of the local spacing */
   uint64_t map_seed;    /* R5: seed of the mapping's integers and phases */
+  int geom;             /* GEOM_BOX or GEOM_CYLINDER (R14) */
 } orc_grid;
 
 typedef struct {
   double mach, re, gamma, pr, prt, cs, k2, k4, sigma, s1, r0, theta, noise;
   int ic;
+  int sgs; /* R10: 0 Smagorinsky, 1 Vreman */
 } orc_flow;
 
 /* ------------------------------------------------------------------------ */
@@ -88,17 +108,38 @@ static ptrdiff_t stride(const orc_grid* g, int d) {
   return d == 0 ? 1 : (d == 1 ? pext(g, 0) : pext(g, 0) * pext(g, 1));
 }
 
-/* lowest / highest node that receives the Runge-Kutta update (R8) */
+static int is_cyl(const orc_grid* g) { return g->geom == GEOM_CYLINDER; }
+
+/* number of distinct nodes of a periodic direction: n, or n - 1 for the
+ * azimuthal direction of a cylindrical grid (first and last coincide, R14) */
+static int period(const orc_grid* g, int d) { return (is_cyl(g) && d == 2) ? ndim(g, d) - 1 : ndim(g, d); }
+
+/* lowest / highest node that receives the Runge-Kutta update (R8, R14) */
 static int interior_lo(const orc_grid* g, int d) { return is_periodic(g, d) ? 0 : 1; }
-static int interior_hi(const orc_grid* g, int d) { return is_periodic(g, d) ? ndim(g, d) - 1 : ndim(g, d) - 2; }
+static int interior_hi(const orc_grid* g, int d) { return is_periodic(g, d) ? period(g, d) - 1 : ndim(g, d) - 2; }
 
 /* the grid node whose value a ghost index holds: wrap or clamp (R8) */
 static int map_index(const orc_grid* g, int d, int idx) {
   int n = ndim(g, d);
-  if (is_periodic(g, d)) return ((idx % n) + n) % n;
+  if (is_periodic(g, d)) {
+    int P = period(g, d);
+    return ((idx % P) + P) % P;
+  }
   if (idx < 0) return 0;
   if (idx > n - 1) return n - 1;
   return idx;
+}
+
+/* the grid node a padded index (i, j, k) holds: behind the centreline of a
+ * cylindrical grid the node across it (R14), else direction by direction */
+static void map_node(const orc_grid* g, int* i, int* j, int* k) {
+  if (is_cyl(g) && *j < 0) {
+    *j = -*j;
+    *k += period(g, 2) / 2;
+  }
+  *i = map_index(g, 0, *i);
+  *j = map_index(g, 1, *j);
+  *k = map_index(g, 2, *k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -136,10 +177,22 @@ static double stretch_G(const orc_grid* g, double H, double s) {
                                    tanh((H * s + g->cluster_r) / g->stretch_w));
 }
 
-/* unmapped coordinate of direction d at (possibly ghost) index idx */
+/* unmapped coordinate of direction d at (possibly ghost) index idx; on a
+ * cylindrical grid direction 1 gives the radius r in [0, hi[1]] (the same
+ * odd clustering function on s = j / (nj - 1), so r(-j) = -r(j)) and
+ * direction 2 the azimuth 2 pi (k mod P) / P */
 double orc_base_coord(const orc_grid* g, int d, double idx) {
   int n = ndim(g, d);
   double lo = g->lo[d], hi = g->hi[d];
+  if (is_cyl(g) && d == 1) {
+    double s = idx / (n - 1);
+    if (g->stretch_c == 0.0) return hi * s;
+    return hi * stretch_G(g, hi, s) / stretch_G(g, hi, 1.0);
+  }
+  if (is_cyl(g) && d == 2) {
+    int P = period(g, 2), kk = (int)idx;
+    return 2.0 * PI * (double)(((kk % P) + P) % P) / P;
+  }
   if (is_periodic(g, d)) return lo + (hi - lo) * idx / n;
   if (d == 0 || g->stretch_c == 0.0) return lo + (hi - lo) * idx / (n - 1);
   double H = 0.5 * (hi - lo), C = 0.5 * (hi + lo);
@@ -159,6 +212,13 @@ void orc_coords(const orc_grid* g, double* X) {
     for (int j = -NG; j < g->nj + NG; ++j)
       for (int i = -NG; i < g->ni + NG; ++i) {
         int idx[3] = {i, j, k};
+        if (is_cyl(g)) { /* R14: x axial, (y, z) = r (cos theta, sin theta) */
+          double r = orc_base_coord(g, 1, j), th = orc_base_coord(g, 2, k);
+          X[at(g, i, j, k)] = orc_base_coord(g, 0, i);
+          X[np + at(g, i, j, k)] = r * cos(th);
+          X[2 * np + at(g, i, j, k)] = r * sin(th);
+          continue;
+        }
         for (int d = 0; d < 3; ++d) {
           double base = orc_base_coord(g, d, idx[d]);
           double x = base;
@@ -185,7 +245,8 @@ static void fill_ghosts(const orc_grid* g, double* F, int ncomp) {
   for (int k = -NG; k < g->nk + NG; ++k)
     for (int j = -NG; j < g->nj + NG; ++j)
       for (int i = -NG; i < g->ni + NG; ++i) {
-        int mi = map_index(g, 0, i), mj = map_index(g, 1, j), mk = map_index(g, 2, k);
+        int mi = i, mj = j, mk = k;
+        map_node(g, &mi, &mj, &mk);
         if (mi == i && mj == j && mk == k) continue;
         for (int c = 0; c < ncomp; ++c)
           F[(size_t)c * np + at(g, i, j, k)] = F[(size_t)c * np + at(g, mi, mj, mk)];
@@ -225,6 +286,9 @@ void orc_metrics(const orc_grid* g, const double* X, double* S /* 9 x npad */, d
                      A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
         J[n] = 1.0 / det;
       }
+  if (is_cyl(g)) /* R15: the centreline takes J of the adjacent radial node */
+    for (int k = 0; k < g->nk; ++k)
+      for (int i = 0; i < g->ni; ++i) J[at(g, i, 0, k)] = J[at(g, i, 1, k)];
   fill_ghosts(g, S, 9);
   fill_ghosts(g, J, 1);
 }
@@ -334,21 +398,29 @@ void orc_apply_bc(const orc_grid* g, const orc_flow* f, const double* X, const d
         if (g->bc[face] == BC_INFLOW) {
           double y = X[np + n], z = X[2 * np + n];
           conserved(f, 1.0, orc_jet_profile(f, sqrt(y * y + z * z)), 0.0, 0.0, 1.0 / f->gamma, qb);
+        } else if (g->bc[face] == BC_AXIS) { /* R14: azimuthal mean of the eta = 1 line */
+          int P = period(g, 2);
+          for (int v = 0; v < 5; ++v) {
+            double s = 0.0;
+            for (int kk = 0; kk < P; ++kk) s += Q[(size_t)v * np + at(g, i, 1, kk)];
+            qb[v] = s / P;
+          }
         } else {
           int ci[3];
           for (int d = 0; d < 3; ++d) {
             ci[d] = idx[d];
-            if (!is_periodic(g, d)) {
-              if (ci[d] < 1) ci[d] = 1;
-              if (ci[d] > ndim(g, d) - 2) ci[d] = ndim(g, d) - 2;
-            }
+            if (ci[d] < interior_lo(g, d)) ci[d] = interior_lo(g, d);
+            if (ci[d] > interior_hi(g, d)) ci[d] = interior_hi(g, d);
           }
           size_t c = at(g, ci[0], ci[1], ci[2]);
           double qi[5], nrm[3];
           for (int v = 0; v < 5; ++v) qi[v] = Q[(size_t)v * np + c];
           int d = face / 2;
           double sgn = (face % 2 == 0) ? -1.0 : 1.0;
-          double a = S[(size_t)(3 * d) * np + n], b = S[(size_t)(3 * d + 1) * np + n], cc = S[(size_t)(3 * d + 2) * np + n];
+          /* R15: on the centreline the face metric vanishes; the normal is
+           * that of the adjacent radial node */
+          size_t nn = (is_cyl(g) && j == 0) ? at(g, i, 1, k) : n;
+          double a = S[(size_t)(3 * d) * np + nn], b = S[(size_t)(3 * d + 1) * np + nn], cc = S[(size_t)(3 * d + 2) * np + nn];
           double len = sqrt(a * a + b * b + cc * cc);
           nrm[0] = sgn * a / len; nrm[1] = sgn * b / len; nrm[2] = sgn * cc / len;
           orc_riemann_farfield(f, qi, nrm, qb);
@@ -442,8 +514,8 @@ static void sweep_inviscid(const orc_grid* g, const double* Q, const double* S, 
       }
 }
 
-/* Viscous flux with Smagorinsky SGS viscosity (Eqs. q_mod, sutherland,
- * tau_mod; R10).  Cartesian gradients at the node:
+/* Viscous flux with Smagorinsky or Vreman SGS viscosity (Eqs. q_mod,
+ * sutherland, tau_mod; R10).  Cartesian gradients at the node:
  *   d phi / d x_m = J sum_k S^k_m d_k phi     (central d_k, Delta xi = 1)
  *   F_m = [0, tau_1m, tau_2m, tau_3m, u_i tau_im - q_m],  q_m = -kappa dT/dx_m
  *   F^k = sum_m S^k_m F_m */
@@ -471,16 +543,34 @@ static void sweep_viscous(const orc_grid* g, const orc_flow* f, const double* S,
           }
         double rho = W[n], T = W[5 * np + n];
         double u[3] = {W[np + n], W[2 * np + n], W[3 * np + n]};
-        /* Smagorinsky eddy viscosity */
-        double Sm2 = 0.0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            double sab = 0.5 * (grad[a][b] + grad[b][a]);
-            Sm2 += sab * sab;
-          }
-        double Smag = sqrt(2.0 * Sm2);
         double delta = pow(J[n], -1.0 / 3.0);
-        double mu_t = rho * (f->cs * delta) * (f->cs * delta) * Smag;
+        double mu_t;
+        if (f->sgs == 1) {
+          /* Vreman: alpha_ij = du_j/dx_i = grad[j][i], beta = Delta^2 alpha^T alpha,
+           * B_beta = sum of the principal 2x2 minors of beta,
+           * mu_t = rho c sqrt(B_beta / (alpha_ij alpha_ij)), c = 2.5 C_s^2 */
+          double beta[3][3], aa = 0.0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double s = 0.0;
+              for (int m = 0; m < 3; ++m) s += grad[a][m] * grad[b][m]; /* alpha_ma alpha_mb */
+              beta[a][b] = delta * delta * s;
+              aa += grad[a][b] * grad[a][b];
+            }
+          double Bb = beta[0][0] * beta[1][1] - beta[0][1] * beta[0][1] + beta[0][0] * beta[2][2] -
+                      beta[0][2] * beta[0][2] + beta[1][1] * beta[2][2] - beta[1][2] * beta[1][2];
+          mu_t = aa > 0.0 ? rho * 2.5 * f->cs * f->cs * sqrt(fmax(Bb, 0.0) / aa) : 0.0;
+        } else {
+          /* Smagorinsky */
+          double Sm2 = 0.0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double sab = 0.5 * (grad[a][b] + grad[b][a]);
+              Sm2 += sab * sab;
+            }
+          double Smag = sqrt(2.0 * Sm2);
+          mu_t = rho * (f->cs * delta) * (f->cs * delta) * Smag;
+        }
         double mu = orc_sutherland(f, T);
         double mu_e = mu + mu_t;
         double kappa = Cp * (mu / f->pr + mu_t / f->prt);
@@ -525,8 +615,8 @@ static void sweep_dissipation_coeffs(const orc_grid* g, const orc_flow* f, const
         for (int kd = 0; kd < 3; ++kd) {
           double sum = 1.0;
           for (int o = 0; o < 3; ++o)
-            if (o != kd) sum += pow(lam[o] / lam[kd], f->sigma);
-          lt[(size_t)kd * np + n] = lam[kd] * sum;
+            if (o != kd && lam[kd] > 0.0) sum += pow(lam[o] / lam[kd], f->sigma);
+          lt[(size_t)kd * np + n] = lam[kd] * sum; /* R15: 0 where lambda^k = 0 */
           ptrdiff_t s = stride(g, kd);
           const double* p = W + 4 * np;
           nu[(size_t)kd * np + n] = fabs(p[n + s] - 2.0 * p[n] + p[n - s]) / (p[n + s] + 2.0 * p[n] + p[n - s]);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_stage_pair.cu", "jz_stage_v.cu", "jz_static.cu", "jz_peak.cu", "jz_stats.cu"]
+SOURCES = ["jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_stage_v.cu", "jz_static.cu", "jz_peak.cu", "jz_stats.cu"]
 
 
 def nvcc() -> str:

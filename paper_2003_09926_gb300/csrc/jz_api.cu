@@ -454,7 +454,8 @@ int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
   if (!f) return fail(JZ_EINVAL, "null flow parameters");
   if (!(f->gamma > 1.0) || !(f->pr > 0.0) || !(f->prt > 0.0) || !(f->mach >= 0.0) || !(f->k2 >= 0.0) ||
       !(f->k4 >= 0.0) || !(f->sigma > 0.0) || !(f->s1 > 0.0) || !(f->cs >= 0.0) || !(f->theta > 0.0) ||
-      !std::isfinite(f->re) || (f->ic != JZ_IC_JET && f->ic != JZ_IC_QUIESCENT))
+      !std::isfinite(f->re) || (f->ic != JZ_IC_JET && f->ic != JZ_IC_QUIESCENT) ||
+      (f->sgs != JZ_SGS_SMAGORINSKY && f->sgs != JZ_SGS_VREMAN))
     return fail(JZ_EINVAL, "bad flow parameters");
   g->flow = *f;
   g->have_flow = true;
@@ -475,6 +476,7 @@ int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
   F.theta = f->theta;
   F.noise = f->noise;
   F.ic = f->ic;
+  F.sgs = f->sgs;
   F.viscous = (F.mu_inf > 0.0 || F.cs > 0.0) ? 1 : 0;
   if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
   if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
@@ -627,8 +629,8 @@ int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc) {
 
 int jz_set_stage_variant(jz_grid* g, int variant) {
   if (int rc = check_grid(g, false)) return rc;
-  if (variant < 0 || variant > 2) return fail(JZ_EINVAL, "stage variant must be 0, 1 or 2");
-  if (variant != 0 && g->dev.prec != JZ_P32) return fail(JZ_EINVAL, "stage variants 1 and 2 are FP32 (JZ_P32) only");
+  if (variant != 0 && variant != 2) return fail(JZ_EINVAL, "stage variant must be 0 or 2");
+  if (variant != 0 && g->dev.prec != JZ_P32) return fail(JZ_EINVAL, "stage variant 2 is FP32 (JZ_P32) only");
   g->dev.variant = variant;
   if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
   if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }

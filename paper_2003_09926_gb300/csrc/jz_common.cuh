@@ -41,6 +41,7 @@ struct FlowC {
   double k2, k4, sigma;   // dissipation constants
   double mach, r0, theta, noise;
   int ic;
+  int sgs;      // JZ_SGS_SMAGORINSKY or JZ_SGS_VREMAN
   int viscous;  // mu_inf > 0 or cs > 0
 };
 

@@ -25,7 +25,7 @@ struct GridDev {
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
   int goff[3], gn[3];  // global index of local node 0 and global node counts (blocks; else 0 and n)
-  int variant;         // stage kernel of P32: 0 scalar, 1 paired FP32x2, 2 vector records
+  int variant;         // stage kernel of P32: 0 scalar records, 2 vector records
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
   CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)

@@ -6,7 +6,7 @@
 // curvilinear coordinates), the anisotropic scalar artificial dissipation
 // (Turkel & Vatsa, pressure sensor, five-point stencil, Section 4.3) and the
 // viscous flux (Stokes stress, Fourier heat flux, Sutherland viscosity,
-// Eqs. q_mod, sutherland, tau_mod) plus a Smagorinsky eddy viscosity, then the
+// Eqs. q_mod, sutherland, tau_mod) plus a Smagorinsky (or Vreman) eddy viscosity, then the
 // update Q^(l) = Q^(0) - alpha_l dt J R(Q^(l-1)) of the 5-stage scheme.
 //
 // Residual in face form.  With G^k = E^k - F^k the contravariant inviscid
@@ -132,12 +132,7 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     }
     const R mu = Fn<R>::div(c.mu_inf * T * Fn<R>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     R mu_t = R(0);
-    if (c.sgs) {  // Smagorinsky: rho (C_s Delta)^2 |S|, Delta = J^(-1/3), |S| = sqrt(2 S_ij S_ij)
-      const R s12 = R(0.5) * (g[0][1] + g[1][0]), s13 = R(0.5) * (g[0][2] + g[2][0]);
-      const R s23 = R(0.5) * (g[1][2] + g[2][1]);
-      const R ss = g[0][0] * g[0][0] + g[1][1] * g[1][1] + g[2][2] * g[2][2] + R(2) * (s12 * s12 + s13 * s13 + s23 * s23);
-      mu_t = rho * c.cs2 * Fn<R>::sqrt_(R(2) * ss) * Fn<R>::jm23(Jn);
-    }
+    if (c.sgs) mu_t = rho * eddy_nu(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
     const R mue = mu + mu_t;
     const R kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
     const R div3 = (g[0][0] + g[1][1] + g[2][2]) * R(2.0 / 3.0);
@@ -624,7 +619,6 @@ cudaError_t stage_configure() {
   if ((e = configure_one<double, double, TI64, TJ64>()) != cudaSuccess) return e;
   if ((e = configure_one<float, double, TIM, TJM>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32>()) != cudaSuccess) return e;
-  if ((e = stage_pair_configure()) != cudaSuccess) return e;
   if ((e = stage_v_configure()) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -634,11 +628,10 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
     case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_one<float, double, TIM, TJM>(g, stage, qsel, qout, s);
     default:
-      if (g.variant == 1 || g.variant == 2) {
+      if (g.variant == 2) {
         StageCtx<float, float> X;
         fill_ctx(X, g);
-        const StageSel st{kRkAlpha[stage], qsel, qout};
-        return g.variant == 1 ? launch_stage_pair(X, st, s) : launch_stage_v(X, st, s);
+        return launch_stage_v(X, StageSel{kRkAlpha[stage], qsel, qout}, s);
       }
       return launch_one<float, float, TI32, TJ32>(g, stage, qsel, qout, s);
   }
@@ -662,8 +655,6 @@ void stage_ctx_fill(void* dst, const GridDev& g) {
 
 cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int4* items, int nitems,
                                unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
-  if (prec == JZ_P32 && variant == 1)
-    return launch_stage_pair_batch(ctx, items, nitems, queue, StageSel{kRkAlpha[stage], qsel, qout}, s);
   if (prec == JZ_P32 && variant == 2)
     return launch_stage_v_batch(ctx, items, nitems, queue, StageSel{kRkAlpha[stage], qsel, qout}, s);
   switch (prec) {

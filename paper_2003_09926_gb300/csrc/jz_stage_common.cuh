@@ -1,4 +1,4 @@
-// jz_stage_common.cuh -- pieces shared by the scalar and the paired (FP32x2)
+// jz_stage_common.cuh -- pieces shared by the scalar and the vector-record
 // fused stage kernels: ring record layout, flow constants in the arithmetic
 // type, elementary-function choices, TMA / mbarrier helpers (inline PTX), the
 // per-grid kernel context and the per-launch stage selection.
@@ -19,6 +19,7 @@ template <typename R>
 struct KConst {
   R gamma, gm1, cp, mu_inf, s1, s1p1, inv_pr, inv_prt, cs2, k2, k4, sigma;
   int viscous, sgs, sig_half;
+  int vreman;  // eddy viscosity of Vreman's model instead of Smagorinsky's
 };
 
 template <typename R>
@@ -39,6 +40,7 @@ __host__ __device__ inline KConst<R> make_kconst(const FlowC& F) {
   c.viscous = F.viscous;
   c.sgs = F.cs > 0.0;
   c.sig_half = F.sigma == 0.5;
+  c.vreman = F.sgs == JZ_SGS_VREMAN;
   return c;
 }
 
@@ -89,28 +91,32 @@ template <> struct Fn<double> {
   }
 };
 
-// Packed FP32 pair: two independent lanes of arithmetic in one FP32x2
-// instruction (fadd/fmul/fma .f32x2).
-struct f2 {
-  float2 v;
-  f2() = default;
-  __device__ __forceinline__ f2(float a) : v(make_float2(a, a)) {}
-  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
-  __device__ __forceinline__ f2(float2 a) : v(a) {}
-};
-
-__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
-// a - b as one packed FMA: b * (-1) + a
-__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
-__device__ __forceinline__ f2 abs2(f2 a) { return f2(fabsf(a.v.x), fabsf(a.v.y)); }
-__device__ __forceinline__ f2 max2(f2 a, f2 b) { return f2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
-__device__ __forceinline__ f2 sqrt2(f2 a) { return f2(Fn<float>::sqrt_(a.v.x), Fn<float>::sqrt_(a.v.y)); }
-__device__ __forceinline__ f2 rcp2(f2 a) { return f2(Fn<float>::rcp(a.v.x), Fn<float>::rcp(a.v.y)); }
-__device__ __forceinline__ f2 jm23_2(f2 a) { return f2(Fn<float>::jm23(a.v.x), Fn<float>::jm23(a.v.y)); }
-__device__ __forceinline__ f2 pow2(f2 a, float e) { return f2(Fn<float>::powp(a.v.x, e), Fn<float>::powp(a.v.y, e)); }
-
+// Eddy viscosity mu_t / rho from the velocity gradients g[a][m] = du_a/dx_m
+// and J (Delta^2 = J^(-2/3)).
+//   Smagorinsky: (C_s Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij).
+//   Vreman (2004): c Delta^2 sqrt(B / (g_am g_am)), c = 2.5 C_s^2, with
+//     b_ab = sum_m g[a][m] g[b][m] and B = b00 b11 - b01^2 + b00 b22 - b02^2
+//     + b11 b22 - b12^2 (the sum of b's principal 2x2 minors, >= 0; clamped at
+//     0 against rounding); 0 where all gradients vanish.
+template <typename R>
+__device__ __forceinline__ R eddy_nu(const KConst<R>& c, const R g[4][3], R Jn) {
+  if (c.vreman) {
+    R b[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int d = a; d < 3; ++d) b[a][d] = g[a][0] * g[d][0] + g[a][1] * g[d][1] + g[a][2] * g[d][2];
+    const R aa = b[0][0] + b[1][1] + b[2][2];
+    const R B = b[0][0] * b[1][1] - b[0][1] * b[0][1] + b[0][0] * b[2][2] - b[0][2] * b[0][2] +
+                b[1][1] * b[2][2] - b[1][2] * b[1][2];
+    if (!(aa > R(0))) return R(0);
+    return R(2.5) * c.cs2 * Fn<R>::jm23(Jn) * Fn<R>::sqrt_(Fn<R>::div(rmax(B, R(0)), aa));
+  }
+  const R s12 = R(0.5) * (g[0][1] + g[1][0]), s13 = R(0.5) * (g[0][2] + g[2][0]);
+  const R s23 = R(0.5) * (g[1][2] + g[2][1]);
+  const R ss = g[0][0] * g[0][0] + g[1][1] * g[1][1] + g[2][2] * g[2][2] + R(2) * (s12 * s12 + s13 * s13 + s23 * s23);
+  return c.cs2 * Fn<R>::sqrt_(R(2) * ss) * Fn<R>::jm23(Jn);
+}
 
 // ---------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX, sm_90+ async proxy)
@@ -215,9 +221,4 @@ cudaError_t stage_v_configure();
 cudaError_t launch_stage_v(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);
 cudaError_t launch_stage_v_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
                                  const stg::StageSel& st, cudaStream_t s);
-// paired FP32x2 kernel for P32 (jz_stage_pair.cu)
-cudaError_t stage_pair_configure();
-cudaError_t launch_stage_pair(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);
-cudaError_t launch_stage_pair_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
-                                    const stg::StageSel& st, cudaStream_t s);
 }  // namespace jz

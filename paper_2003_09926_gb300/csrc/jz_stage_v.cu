@@ -5,7 +5,7 @@
 // sub-step, the centred inviscid flux in general curvilinear coordinates, the
 // Turkel-Vatsa anisotropic scalar artificial dissipation (pressure sensor,
 // five-point stencil, Section 4.3), the viscous flux (Stokes stress, Fourier
-// heat flux, Sutherland viscosity) plus a Smagorinsky eddy viscosity, then
+// heat flux, Sutherland viscosity) plus a Smagorinsky (or Vreman) eddy viscosity, then
 // the update Q^(l) = Q^(0) - alpha_l dt J R(Q^(l-1)) of the 5-stage scheme.
 // The residual is taken in face form, R_n = sum_k (h^k_{n+1/2} - h^k_{n-1/2})
 // with h_{n+1/2} = (G_n + G_{n+1})/2 - d_{n+1/2}, G = E - F the contravariant
@@ -159,13 +159,7 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
       for (int m = 0; m < 3; ++m) g[q][m] = hJ * (S[m] * d0[q] + S[3 + m] * d1[q] + S[6 + m] * d2[q]);
     const float mu = Fn<float>::div(c.mu_inf * T * Fn<float>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     float mu_t = 0.f;
-    if (c.sgs) {  // Smagorinsky: rho (C_s Delta)^2 |S|, Delta = J^(-1/3), |S| = sqrt(2 S_ij S_ij)
-      const float s12 = 0.5f * (g[0][1] + g[1][0]), s13 = 0.5f * (g[0][2] + g[2][0]);
-      const float s23 = 0.5f * (g[1][2] + g[2][1]);
-      const float ss =
-          g[0][0] * g[0][0] + g[1][1] * g[1][1] + g[2][2] * g[2][2] + 2.f * (s12 * s12 + s13 * s13 + s23 * s23);
-      mu_t = rho * c.cs2 * Fn<float>::sqrt_(2.f * ss) * Fn<float>::jm23(Jn);
-    }
+    if (c.sgs) mu_t = rho * eddy_nu(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
     const float mue = mu + mu_t;
     const float kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
     const float div3 = (g[0][0] + g[1][1] + g[2][2]) * (2.f / 3.f);

@@ -39,7 +39,7 @@ class GridDesc(C.Structure):
 class FlowParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in
                 ("mach", "re", "gamma", "pr", "prt", "cs", "k2", "k4", "sigma", "s1", "r0", "theta", "noise")] + [
-        ("ic", C.c_int)]
+        ("ic", C.c_int), ("sgs", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -146,7 +146,7 @@ def make_desc(d: dict) -> GridDesc:
 def make_flow(f: dict) -> FlowParams:
     p = FlowParams()
     for n, _ in FlowParams._fields_:
-        setattr(p, n, f[n])
+        setattr(p, n, f.get(n, 0) if n == "sgs" else f[n])
     return p
 
 

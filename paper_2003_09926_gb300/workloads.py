@@ -13,9 +13,11 @@ import math
 
 import numpy as np
 
-BC_PERIODIC, BC_INFLOW, BC_FARFIELD = 0, 1, 2
+BC_PERIODIC, BC_INFLOW, BC_FARFIELD, BC_AXIS = 0, 1, 2, 4
+GEOM_BOX, GEOM_CYLINDER = 0, 1
 P64, P32_M64, P32 = 0, 1, 2
 IC_JET, IC_QUIESCENT = 0, 1
+SGS_SMAGORINSKY, SGS_VREMAN = 0, 1
 PRECISION_NAMES = {P64: "P64", P32_M64: "P32_M64", P32: "P32"}
 
 JET_BC = [BC_INFLOW, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD]
@@ -27,7 +29,7 @@ def jet_flow(**over) -> dict:
     constants: Sutherland S1 = 110.4 K / 288.15 K, Smagorinsky C_s = 0.18,
     Pr_t = 0.9, Turkel-Vatsa k2 = 1/4, k4 = 1/256, sigma = 1/2)."""
     f = dict(mach=1.4, re=1.57e6, gamma=1.4, pr=0.72, prt=0.9, cs=0.18, k2=0.25, k4=1.0 / 256.0, sigma=0.5,
-             s1=110.4 / 288.15, r0=0.5, theta=0.05, noise=0.01, ic=IC_JET)
+             s1=110.4 / 288.15, r0=0.5, theta=0.05, noise=0.01, ic=IC_JET, sgs=SGS_SMAGORINSKY)
     f.update(over)
     return f
 
@@ -37,6 +39,20 @@ def jet_grid(ni: int, nj: int, nk: int, map_amp: float = 0.0, map_seed: int = 0,
     return dict(ni=ni, nj=nj, nk=nk, bc=list(JET_BC), lo=[0.0, -8.0, -8.0], hi=[30.0, 8.0, 8.0],
                 cluster_r=0.5, stretch_c=0.4, stretch_w=0.5, map_amp=map_amp, map_seed=map_seed,
                 precision=precision)
+
+
+CYL_BC = [BC_INFLOW, BC_FARFIELD, BC_AXIS, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC]
+
+
+def cyl_grid(ni: int, nj: int, nk: int = 361, length: float = 30.0, radius: float = 8.0, stretch_c: float = 0.4,
+             precision: int = P64) -> dict:
+    """The paper's cylindrical jet grid (Section 3, Tab. mesh): xi axial on
+    [0, length], eta radial on [0, radius] from the centreline with the tanh
+    clustering at r = 0.5, zeta azimuthal with nk points (361 in the paper),
+    the first and last coinciding."""
+    return dict(ni=ni, nj=nj, nk=nk, bc=list(CYL_BC), lo=[0.0, 0.0, 0.0], hi=[length, radius, 2.0 * math.pi],
+                cluster_r=0.5, stretch_c=stretch_c, stretch_w=0.5, map_amp=0.0, map_seed=0, precision=precision,
+                geom=GEOM_CYLINDER)
 
 
 def periodic_grid(ni: int, nj: int, nk: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), map_amp: float = 0.0,

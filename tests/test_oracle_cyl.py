@@ -1,0 +1,185 @@
+"""Oracle pins for the paper's cylindrical jet grid (Section 3: a domain of
+cylindrical shape with the centreline singularity, its properties
+extrapolated from the adjacent radial line and averaged in the azimuthal
+direction, and superposed first and last azimuthal points).
+
+Pinned against closed forms (the central-difference Jacobian of a polar
+grid), exact invariants (the discrete metric identity at the nodes next to
+the centreline, free-stream preservation, the half-turn symmetry of an
+axisymmetric state) and a brute-force
+restatement of the centreline and ghost rules."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_09926_gb300 import workloads as W
+
+NG = 2
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def test_cylinder_coordinates(orc):
+    g = W.cyl_grid(10, 9, 21, stretch_c=0.4)
+    o = orc.Oracle(g, W.jet_flow())
+    X = o.X
+    inner = o.inner(X)
+    # the centreline: y = z = 0 exactly for every azimuthal index
+    assert np.abs(inner[1:, :, 0, :]).max() == 0.0
+    # superposed first and last azimuthal planes
+    assert np.array_equal(inner[:, -1], inner[:, 0])
+    # radius of node j: the clustering map on [0, R], increasing
+    r = np.sqrt(inner[1, 0, :, 0] ** 2 + inner[2, 0, :, 0] ** 2)
+    assert np.all(np.diff(r) > 0) and r[-1] == pytest.approx(8.0, rel=1e-15)
+    # ghosts behind the centreline are the points across it: (-j, k + P/2)
+    P = 20
+    for jg in (1, 2):
+        for k in range(-2, 21 + 2):
+            kk = (k + P // 2) % P
+            np.testing.assert_allclose(X[:, k + NG, -jg + NG, :], X[:, kk + NG, jg + NG, :], rtol=0, atol=1e-14)
+
+
+def test_cylinder_jacobian_closed_form(orc):
+    """Uniform radial spacing: x = i dx, y = r cos(theta), z = r sin(theta)
+    with r = j dr, theta = k dtheta.  The central-difference Jacobian matrix
+    is [[dx, 0, 0], [0, dr cos, -r sin sin(dth)], [0, dr sin, r cos sin(dth)]],
+    so 1/J = dx dr r sin(dth) off the centreline; on it J is taken from the
+    adjacent radial node."""
+    ni, nj, nk = 8, 7, 13
+    g = W.cyl_grid(ni, nj, nk, length=3.5, radius=1.5, stretch_c=0.0)
+    o = orc.Oracle(g, W.jet_flow())
+    dx, dr, dth = 3.5 / (ni - 1), 1.5 / (nj - 1), 2 * math.pi / (nk - 1)
+    J = o.inner(o.J)
+    r = dr * np.arange(nj)
+    want = 1.0 / (dx * dr * r[1:] * math.sin(dth))
+    np.testing.assert_allclose(J[:, 1:, :], np.broadcast_to(want[None, :, None], J[:, 1:, :].shape), rtol=1e-13)
+    np.testing.assert_array_equal(J[:, 0, :], J[:, 1, :])
+
+
+def test_cylinder_metric_identity_next_to_the_centreline(orc):
+    """sum_k d_k S^k_m = 0 at every node off the centreline, including the
+    first radial line, whose eta-difference reaches S^eta on the centreline
+    (which the conservative form makes exactly zero)."""
+    g = W.cyl_grid(9, 8, 17, stretch_c=0.4)
+    o = orc.Oracle(g, W.jet_flow())
+    S = o.S
+    assert np.abs(o.inner(S)[3:6, :, 0, :]).max() == 0.0
+    sl = (slice(NG, -NG), slice(NG + 1, -NG - 1), slice(NG + 1, -NG - 1))  # all k, j = 1..nj-2, i = 1..ni-2
+    for m in range(3):
+        div = np.zeros(S.shape[1:])[sl]
+        for kd in range(3):
+            F = S[3 * kd + m]
+            ax = 2 - kd  # array axis of direction kd: (k, j, i)
+            div = div + 0.5 * (np.roll(F, -1, axis=ax) - np.roll(F, 1, axis=ax))[sl]
+        assert np.abs(div).max() <= 1e-13 * np.abs(S[m::3]).max(), m
+
+
+def _uniform_q(shape, rho, u, v, w, p, g=1.4):
+    Q = np.empty((5,) + shape)
+    Q[0] = rho
+    Q[1], Q[2], Q[3] = rho * u, rho * v, rho * w
+    Q[4] = p / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)
+    return Q
+
+
+def test_cylinder_centreline_and_ghost_rules(orc):
+    """Brute force: after the boundary pass, a centreline node (away from the
+    x faces) holds the azimuthal mean of the eta = 1 line (summed in azimuthal
+    order), ghosts behind it the nodes across it, the last azimuthal plane the
+    first, and azimuthal ghosts wrap with period nk - 1."""
+    ni, nj, nk = 9, 7, 13
+    P = nk - 1
+    g = W.cyl_grid(ni, nj, nk)
+    o = orc.Oracle(g, W.jet_flow())
+    rng = np.random.default_rng(4)
+    Q = o.new_state()
+    Q[...] = np.nan
+    Q[:, NG:-NG, NG:-NG, NG:-NG] = W.random_state((nk, nj, ni), seed=9)
+    o.apply_bc(Q)
+    for v in range(5):
+        for i in range(1, ni - 1):
+            s = 0.0
+            for k in range(P):
+                s += Q[v, k + NG, 1 + NG, i + NG]
+            for k in range(nk):
+                assert Q[v, k + NG, NG, i + NG] == s / P
+    assert np.array_equal(Q[:, nk - 1 + NG], Q[:, NG])
+    for k in range(-2, nk + 2):
+        kk = k % P
+        if 0 <= k < nk - 1:
+            continue
+        assert np.array_equal(Q[:, k + NG, NG:-NG, NG:-NG], Q[:, kk + NG, NG:-NG, NG:-NG]), k
+    for jg in (1, 2):
+        for k in range(nk):
+            kk = (k + P // 2) % P
+            assert np.array_equal(Q[:, k + NG, -jg + NG, NG:-NG], Q[:, kk + NG, jg + NG, NG:-NG])
+    assert np.isfinite(Q).all()
+    del rng
+
+
+def test_cylinder_freestream_preserved(orc):
+    """A uniform state with a non-zero velocity: the residual vanishes to
+    rounding at every updated node whose stencil reaches no inflow or
+    far-field node (those hold the jet profile and the Riemann state),
+    including the radial line next to the centreline."""
+    g = W.cyl_grid(10, 8, 17, stretch_c=0.4)
+    f = W.jet_flow(re=5e3)
+    o = orc.Oracle(g, f)
+    Q = o.new_state()
+    Q[:] = _uniform_q(o.shape, 1.0, 0.5, 0.2, -0.15, 1 / 1.4)
+    o.apply_bc(Q)
+    R = o.inner(o.residual(Q))
+    sel = R[:, :-1, 1:-3, 3:-3]  # k < P, j = 1..nj-4, i = 3..ni-4 (the +-2 stencil misses the boundary nodes)
+    scale = np.abs(o.inner(o.S)).max() * np.abs(Q).max()
+    assert np.abs(sel).max() <= 1e-13 * scale
+
+
+def test_cylinder_half_turn_symmetry(orc):
+    """The grid is mapped onto itself by a half turn about the axis (k ->
+    k + P/2), and so are the conservative metric terms (products of two
+    Cartesian coordinates keep their sign; a quarter turn would not keep
+    them).  For an axisymmetric state (density, pressure, axial and radial
+    velocity functions of x and r) the residual at (j, k + P/2) equals the
+    one at (j, k) with its y and z momentum components negated, to rounding,
+    at every updated node; a wrong azimuthal period breaks this near the
+    seam, a missing centreline term near the axis."""
+    ni, nj, nk = 10, 8, 17
+    P = nk - 1
+    g = W.cyl_grid(ni, nj, nk, stretch_c=0.4)
+    f = W.jet_flow(re=2e3)
+    o = orc.Oracle(g, f)
+    X = o.X
+    x, r = X[0], np.sqrt(X[1] ** 2 + X[2] ** 2)
+    th = np.arctan2(X[2], X[1])
+    rho = 1.0 + 0.1 * np.exp(-r * r) * np.cos(0.3 * x)
+    ua = 1.2 * np.exp(-r * r)
+    ur = 0.3 * r * np.exp(-r * r) * np.sin(0.2 * x + 0.4)
+    p = (1.0 + 0.05 * np.exp(-r * r)) / 1.4
+    Q = _uniform_q(o.shape, rho, ua, ur * np.cos(th), ur * np.sin(th), p)
+    o.apply_bc(Q)
+    R = o.inner(o.residual(Q))[:, :P]
+    Rh = np.roll(R, -P // 2, axis=1)  # Rh[:, k] = R[:, k + P/2]
+    sgn = np.array([1, 1, -1, -1, 1])[:, None, None, None]
+    sel = (slice(None), slice(None), slice(1, -1), slice(1, -1))
+    scale = np.abs(R[sel]).max(axis=(1, 2, 3))[:, None, None, None]
+    assert np.all(scale > 0)
+    assert np.abs((Rh - sgn * R)[sel] / scale).max() <= 1e-11
+
+
+def test_cylinder_jet_runs_and_keeps_its_invariants(orc):
+    g = W.cyl_grid(16, 10, 25)
+    o = orc.Oracle(g, W.jet_flow())
+    Q = o.init(2)
+    o.run(Q, 10, cfl=0.5)
+    I = o.inner(Q)
+    assert np.isfinite(I).all() and o.last_dt > 0
+    assert np.array_equal(I[:, -1], I[:, 0])
+    assert np.abs(I[:, :, 0, 1:-1] - I[:, :1, 0, 1:-1]).max() == 0.0
+    d = o.diagnostics(Q)
+    assert 0.9 < d["rho_min"] <= d["rho_max"] < 1.1 and d["mach_max"] < 1.6

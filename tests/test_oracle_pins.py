@@ -369,6 +369,93 @@ def test_smagorinsky_pure_shear_exact(orc):
     assert np.abs(2 * (f["cs"] * h) ** 2 * a * (a * Y + b)).min() > 0.01 * mu * a
 
 
+def test_vreman_vanishes_in_pure_shear(orc):
+    """Vreman's model gives no eddy viscosity in pure shear: with
+    u = (a y^2/2 + b y, 0, 0) only du/dy is non-zero, b_ij has one non-zero
+    entry and all its 2x2 minors vanish, so the x-momentum residual is the
+    laminar -(1/J) mu a (where Smagorinsky adds 2 (C_s h)^2 a (a y + b))."""
+    h, a, b = 0.1, 0.7, 2.0
+    d = W.periodic_grid(7, 7, 7, hi=(0.6, 0.6, 0.6))
+    d["bc"] = [W.BC_FARFIELD] * 6
+    f = W.jet_flow(re=100.0, cs=0.18, k2=0.0, k4=0.0, sgs=W.SGS_VREMAN)
+
+    def fields(X, Y, Z):
+        one = np.ones_like(X)
+        return one, a * Y * Y / 2 + b * Y, 0 * one, 0 * one, one / 1.4
+
+    o, Rv = _viscous_part(orc, d, f, fields)
+    mu = f["mach"] / f["re"]
+    got = _interior(o, Rv)[1]
+    np.testing.assert_allclose(got, np.full(got.shape, -h ** 3 * mu * a), rtol=1e-12)
+
+
+def test_vreman_linear_field_matches_invariant_form(orc):
+    """u = A x (a general constant gradient g = A), rho = 1, T = 1, cube grid
+    (Delta = h).  Vreman: nu_t = 2.5 C_s^2 h^2 sqrt(B / |A|^2), B the second
+    invariant of M = A A^T, here taken as ((tr M)^2 - tr(M^2)) / 2 instead of
+    the sum of principal minors.  The stress is constant, so the momentum
+    residual vanishes and the energy residual is the exact centred difference
+    of the linear u_a tau_am: -(1/J) (mu + nu_t) A_am (A_am + A_ma - 2/3 tr A delta_am)."""
+    h = 0.1
+    d = W.periodic_grid(7, 7, 7, hi=(0.6, 0.6, 0.6))
+    d["bc"] = [W.BC_FARFIELD] * 6
+    f = W.jet_flow(re=1000.0, cs=0.18, k2=0.0, k4=0.0, sgs=W.SGS_VREMAN)
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        A = rng.uniform(-2, 2, size=(3, 3))
+
+        def fields(X, Y, Z):
+            one = np.ones_like(X)
+            u = [A[c, 0] * X + A[c, 1] * Y + A[c, 2] * Z for c in range(3)]
+            return one, u[0], u[1], u[2], one / 1.4
+
+        o, Rv = _viscous_part(orc, d, f, fields)
+        M = A @ A.T
+        B = (np.trace(M) ** 2 - np.trace(M @ M)) / 2
+        nut = 2.5 * f["cs"] ** 2 * h * h * np.sqrt(B / np.trace(M))
+        mu = f["mach"] / f["re"]
+        S = A + A.T - 2.0 / 3.0 * np.trace(A) * np.eye(3)
+        expE = -h ** 3 * (mu + nut) * np.sum(A * S)
+        got = _interior(o, Rv)[4]
+        np.testing.assert_allclose(got, np.full(got.shape, expE), rtol=1e-11)
+        for c in range(3):
+            assert np.abs(_interior(o, Rv)[1 + c]).max() <= 1e-14
+        assert nut > 0.2 * mu  # the eddy viscosity is a sizeable part of the check
+
+
+def test_vreman_shear_plus_rotation_closed_form(orc):
+    """u = (a y^2/2 + b y, c x, 0): s = a y + b and c are the only gradients,
+    B = s^2 c^2, so nu_V(y) = 2.5 C_s^2 h^2 |c| s / sqrt(s^2 + c^2) (s > 0);
+    tau_xy = (mu + nu_V)(s + c).  Node gradients are exact (quadratic u,
+    linear v), so the x-momentum residual is -h^3 D_y[tau_xy], the
+    y-momentum residual vanishes, and the energy residual is
+    -h^3 [c tau_xy + D_y(u tau_xy)], D_y the centred difference."""
+    h, a, b, c = 0.1, 0.9, 1.5, -2.0
+    d = W.periodic_grid(7, 7, 7, hi=(0.6, 0.6, 0.6))
+    d["bc"] = [W.BC_FARFIELD] * 6
+    f = W.jet_flow(re=1000.0, cs=0.18, k2=0.0, k4=0.0, sgs=W.SGS_VREMAN)
+
+    def fields(X, Y, Z):
+        one = np.ones_like(X)
+        return one, a * Y * Y / 2 + b * Y, c * X, 0 * one, one / 1.4
+
+    o, Rv = _viscous_part(orc, d, f, fields)
+    mu = f["mach"] / f["re"]
+    Y = _interior(o, o.X)[1]
+
+    def tau(y):
+        s = a * y + b
+        return (mu + 2.5 * f["cs"] ** 2 * h * h * abs(c) * s / np.sqrt(s * s + c * c)) * (s + c)
+
+    def ut(y):
+        return (a * y * y / 2 + b * y) * tau(y)
+
+    D = lambda fn: (fn(Y + h) - fn(Y - h)) / (2 * h)
+    np.testing.assert_allclose(_interior(o, Rv)[1], -h ** 3 * D(tau), rtol=1e-11)
+    assert np.abs(_interior(o, Rv)[2]).max() <= 1e-15
+    np.testing.assert_allclose(_interior(o, Rv)[4], -h ** 3 * (c * tau(Y) + D(ut)), rtol=1e-11)
+
+
 def test_heat_flux_with_sgs_prandtl(orc):
     """T linear in x (rho = 1), u = (b y, 0, 0): grad T and |S| = b are exact,
     mu_e(x) = mu(T(x)) + (C_s h)^2 b, kappa_e = Cp (mu/Pr + mu_t/Pr_t).
