@@ -54,6 +54,11 @@ extern "C" {
 #define JZ_BC_PERIODIC 0
 #define JZ_BC_INFLOW 1   /* jet exit plane: fixed top-hat profile (Section 3) */
 #define JZ_BC_FARFIELD 2 /* Riemann invariants against air at rest (Section 3) */
+#define JZ_BC_AXIS 4     /* centreline of a cylindrical grid (y- face only)     */
+
+/* grid geometry */
+#define JZ_GEOM_BOX 0      /* Cartesian box, optional tanh clustering and mapping */
+#define JZ_GEOM_CYLINDER 1 /* the paper's cylindrical jet grid (Section 3)        */
 
 /* precision modes: state/flux arithmetic, metric storage */
 #define JZ_P64 0     /* FP64 state and fluxes, FP64 metrics                   */
@@ -76,11 +81,28 @@ extern "C" {
 
 /* Grid descriptor.  Nodes are numbered 0..n-1 per direction (i fastest);
  * non-periodic directions need n >= 3 and their first and last nodes are
- * boundary nodes set by the boundary conditions.  Coordinates: x is uniform
- * on [lo[0], hi[0]]; y and z (when not periodic and stretch_c > 0) follow a
- * tanh clustering about |y| = cluster_r; every coordinate then receives a
- * seeded sinusoidal offset of amplitude map_amp x local spacing (0 = none).
- * Periodic directions use uniform spacing (hi - lo)/n. */
+ * boundary nodes set by the boundary conditions.
+ *
+ * JZ_GEOM_BOX: x is uniform on [lo[0], hi[0]]; y and z (when not periodic
+ * and stretch_c > 0) follow a tanh clustering about |y| = cluster_r; every
+ * coordinate then receives a seeded sinusoidal offset of amplitude
+ * map_amp x local spacing (0 = none).  Periodic directions use uniform
+ * spacing (hi - lo)/n.
+ *
+ * JZ_GEOM_CYLINDER (Section 3, Tab. mesh): i axial (x uniform on
+ * [lo[0], hi[0]]), j radial from the centreline, r in [0, hi[1]] with the
+ * same tanh clustering about r = cluster_r (lo[1] must be 0), k azimuthal,
+ * theta = 2 pi (k mod P) / P with P = nk - 1: the first and last azimuthal
+ * nodes coincide (the paper uses nk = 361).  y = r cos(theta),
+ * z = r sin(theta).  Faces: bc[2] = JZ_BC_AXIS, bc[4] = bc[5] =
+ * JZ_BC_PERIODIC, bc[0], bc[1], bc[3] inflow or far field; P even (the
+ * ghosts behind the centreline are the nodes across it, k + P/2), nk >= 5,
+ * nj >= 4, map_amp = 0.  Centreline nodes hold the mean over the P
+ * distinct azimuthal nodes of the adjacent radial line (summed in
+ * azimuthal order, in FP64); the last azimuthal plane holds a copy of the
+ * first; J on the centreline (where the conservative metric form gives zero
+ * volume) is that of the adjacent radial node.  Blocks of a cylindrical grid
+ * may split direction i only. */
 typedef struct jz_grid_desc {
   int ni, nj, nk;
   int bc[6];
@@ -89,6 +111,7 @@ typedef struct jz_grid_desc {
   double map_amp;
   uint64_t map_seed;
   int precision; /* JZ_P64, JZ_P32_M64 or JZ_P32 */
+  int geom;      /* JZ_GEOM_BOX or JZ_GEOM_CYLINDER */
 } jz_grid_desc;
 
 /* Flow parameters.  re <= 0 means inviscid (no molecular viscosity);

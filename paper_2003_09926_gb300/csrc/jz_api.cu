@@ -57,7 +57,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Carve {
   Layout L;
   size_t es, ms;  // state / metric element sizes
-  size_t off_sc, off_partial, off_tab, off_inflow, off_q0, off_qa, off_qb, off_m, total;
+  size_t off_sc, off_partial, off_tab, off_inflow, off_axis, off_q0, off_qa, off_qb, off_m, total;
   size_t tab_len;
 };
 
@@ -67,7 +67,7 @@ static int validate(const jz_grid_desc* d) {
   for (int a = 0; a < 3; ++a) {
     int b0 = d->bc[2 * a], b1 = d->bc[2 * a + 1];
     for (int b : {b0, b1})
-      if (b != JZ_BC_PERIODIC && b != JZ_BC_INFLOW && b != JZ_BC_FARFIELD)
+      if (b != JZ_BC_PERIODIC && b != JZ_BC_INFLOW && b != JZ_BC_FARFIELD && b != JZ_BC_AXIS)
         return fail(JZ_EINVAL, "bad boundary kind %d", b);
     if ((b0 == JZ_BC_PERIODIC) != (b1 == JZ_BC_PERIODIC))
       return fail(JZ_EINVAL, "direction %d: both faces or neither must be periodic", a);
@@ -83,6 +83,21 @@ static int validate(const jz_grid_desc* d) {
   if (d->stretch_c != 0.0 && !(d->stretch_w > 0.0)) return fail(JZ_EINVAL, "stretch_w must be > 0");
   if (!std::isfinite(d->map_amp) || !std::isfinite(d->stretch_c) || !std::isfinite(d->cluster_r))
     return fail(JZ_EINVAL, "non-finite grid parameter");
+  if (d->geom != JZ_GEOM_BOX && d->geom != JZ_GEOM_CYLINDER) return fail(JZ_EINVAL, "bad geometry %d", d->geom);
+  for (int f = 0; f < 6; ++f)
+    if (d->bc[f] == JZ_BC_AXIS && !(f == 2 && d->geom == JZ_GEOM_CYLINDER))
+      return fail(JZ_EINVAL, "the centreline condition is the y- face of a cylindrical grid only");
+  if (d->geom == JZ_GEOM_CYLINDER) {
+    if (d->bc[2] != JZ_BC_AXIS) return fail(JZ_EINVAL, "a cylindrical grid needs JZ_BC_AXIS on its y- face");
+    if (d->bc[4] != JZ_BC_PERIODIC) return fail(JZ_EINVAL, "a cylindrical grid is periodic in k");
+    if (d->bc[0] == JZ_BC_PERIODIC || d->bc[3] == JZ_BC_PERIODIC)
+      return fail(JZ_EINVAL, "a cylindrical grid is not periodic in i or j");
+    if (d->nk < 5 || (d->nk - 1) % 2 != 0)
+      return fail(JZ_EINVAL, "a cylindrical grid needs nk - 1 even and nk >= 5 (got %d)", d->nk);
+    if (d->nj < 4) return fail(JZ_EINVAL, "a cylindrical grid needs nj >= 4");
+    if (d->lo[1] != 0.0) return fail(JZ_EINVAL, "a cylindrical grid's radius starts at lo[1] = 0");
+    if (d->map_amp != 0.0) return fail(JZ_EINVAL, "a cylindrical grid takes no sinusoidal mapping");
+  }
   return JZ_OK;
 }
 
@@ -101,6 +116,8 @@ static int validate_block(const jz_grid_desc* d, const int* o0, const int* o1) {
                   gn[a] - 1);
     const bool split = o0[a] > 0 || o1[a] < gn[a] - 1;
     if (split && d->bc[2 * a] == JZ_BC_PERIODIC) return fail(JZ_EINVAL, "direction %d: a periodic direction cannot be split", a);
+    if (split && a > 0 && d->geom == JZ_GEOM_CYLINDER)
+      return fail(JZ_EINVAL, "direction %d: a cylindrical grid may be split in i only", a);
     if (split && o1[a] - o0[a] + 1 < 3)
       return fail(JZ_EINVAL, "direction %d: a block of a split direction needs at least 3 nodes", a);
   }
@@ -115,11 +132,14 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
     const int b0 = o0 ? o0[a] : 0, b1 = o1 ? o1[a] : gn[a] - 1;
     L.n[a] = b1 - b0 + 1;
     L.per[a] = d->bc[2 * a] == JZ_BC_PERIODIC;
+    // azimuth of a cylinder: the last node repeats the first
+    L.pn[a] = (d->geom == JZ_GEOM_CYLINDER && a == 2) ? L.n[a] - 1 : L.n[a];
     L.bc[2 * a] = b0 > 0 ? BC_EXCHANGE : d->bc[2 * a];
     L.bc[2 * a + 1] = b1 < gn[a] - 1 ? BC_EXCHANGE : d->bc[2 * a + 1];
     L.lo[a] = (L.per[a] || L.bc[2 * a] == BC_EXCHANGE) ? 0 : 1;
-    L.hi[a] = (L.per[a] || L.bc[2 * a + 1] == BC_EXCHANGE) ? L.n[a] - 1 : L.n[a] - 2;
+    L.hi[a] = L.per[a] ? L.pn[a] - 1 : (L.bc[2 * a + 1] == BC_EXCHANGE ? L.n[a] - 1 : L.n[a] - 2);
   }
+  L.cyl = d->geom == JZ_GEOM_CYLINDER;
   L.pitch = ((L.n[0] + 2 * NG) + 31) / 32 * 32;
   L.plane = (long long)L.pitch * (L.n[1] + 2 * NG);
   L.npad = L.plane * (L.n[2] + 2 * NG);
@@ -127,11 +147,13 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
   c.ms = d->precision == JZ_P32 ? 4 : 8;
   c.tab_len = 0;
   for (int a = 0; a < 3; ++a) c.tab_len += 5 * (size_t)(L.n[a] + 2 * NG);
+  c.tab_len += 2 * (size_t)(L.n[2] + 2 * NG);  // azimuth cos / sin
   size_t off = 0;
   c.off_sc = off; off = align256(off + sizeof(Scalars));
   c.off_partial = off; off = align256(off + sizeof(double) * RED_BLOCKS * DIAG_WORDS);
   c.off_tab = off; off = align256(off + sizeof(double) * c.tab_len);
   c.off_inflow = off; off = align256(off + sizeof(double) * (size_t)L.n[1] * (size_t)L.n[2]);
+  c.off_axis = off; off = align256(off + sizeof(double) * 5 * (size_t)(L.cyl ? L.n[0] : 1));
   size_t qbytes = align256(5 * (size_t)L.npad * c.es);
   c.off_q0 = off; off += qbytes;
   c.off_qa = off; off += qbytes;
@@ -177,6 +199,7 @@ struct jz_batch {
   char* dev = nullptr;
   size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0;
   int nitems = 0, bc_blocks = 1;
+  bool cyl = false;             // some grid is cylindrical (centreline means before each boundary pass)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   double graph_cfl = -1.0;
@@ -377,6 +400,7 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
   d.sc = (Scalars*)(g->base + cv.off_sc);
   d.partial = (double*)(g->base + cv.off_partial);
   d.inflow = (double*)(g->base + cv.off_inflow);
+  d.axis = (double*)(g->base + cv.off_axis);
   d.kc = default_kc(cv.L, d.prec);
   d.variant = d.prec == JZ_P32 ? 2 : 0;  // P32: the vector-record kernel (fastest measured)
   const int gn[3] = {desc->ni, desc->nj, desc->nk};
@@ -394,16 +418,21 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
   }
   for (int a = 0; a < 3; ++a)
     for (int e = 0; e < 3; ++e) { d.C.sn[a][e] = tab + off; off += cv.L.n[e] + 2 * NG; }
+  d.C.cth = tab + off; off += cv.L.n[2] + 2 * NG;
+  d.C.sth = tab + off; off += cv.L.n[2] + 2 * NG;
   d.C.amp = desc->map_amp;
+  d.C.cyl = cv.L.cyl;
   TabParams tp;
   for (int a = 0; a < 3; ++a) {
     tp.n[a] = cv.L.n[a];
     tp.off[a] = d.goff[a];
     tp.gn[a] = d.gn[a];
     tp.per[a] = cv.L.per[a];
+    tp.pn[a] = cv.L.pn[a];
     tp.lo[a] = desc->lo[a];
     tp.hi[a] = desc->hi[a];
   }
+  tp.cyl = cv.L.cyl;
   tp.cluster_r = desc->cluster_r;
   tp.stretch_c = desc->stretch_c;
   tp.stretch_w = desc->stretch_w;
@@ -790,7 +819,7 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
     e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
                            (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
-    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], s);
+    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], b->cyl, s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched boundary launch failed: %s", cudaGetErrorString(e));
     if (b->coupled && l < 4)
       if (int rc = enqueue_exchange(b, out[l])) return rc;
@@ -833,6 +862,7 @@ int create_batch(jz_grid* const* grids, int n, bool coupled, void* dev_buf, size
   b->off_queue = P.off_queue;
   b->nitems = (int)P.items.size();
   b->bc_blocks = nb;
+  for (int k = 0; k < n; ++k) b->cyl = b->cyl || grids[k]->dev.L.cyl;
   b->coupled = coupled;
   b->off_x = P.off_x;
   for (int d = 0; d < 3; ++d) {

@@ -27,9 +27,30 @@ struct Layout {
   long long npad;    // elements per field
   int lo[3], hi[3];  // range of nodes updated by the Runge-Kutta stages
   int per[3];        // periodic flags
+  int pn[3];         // distinct nodes of a periodic direction (n; n - 1 azimuthally on a cylinder)
   int bc[6];         // boundary kind per face
+  int cyl;           // cylindrical grid: centreline at j = 0, azimuth k
   __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
     return (long long)(i + NG) + (long long)(j + NG) * pitch + (long long)(k + NG) * plane;
+  }
+  // the grid node whose value a padded index holds: wrap with the period,
+  // else clamp onto the first / last node
+  __host__ __device__ __forceinline__ int map1(int d, int idx) const {
+    if (per[d]) {
+      const int r = idx % pn[d];
+      return r < 0 ? r + pn[d] : r;
+    }
+    return idx < 0 ? 0 : (idx > n[d] - 1 ? n[d] - 1 : idx);
+  }
+  // ... and across the centreline of a cylindrical grid: (i, -j, k + P/2)
+  __host__ __device__ __forceinline__ void map_node(int& i, int& j, int& k) const {
+    if (cyl && j < 0) {
+      j = -j;
+      k += pn[2] / 2;
+    }
+    i = map1(0, i);
+    j = map1(1, j);
+    k = map1(2, k);
   }
 };
 
@@ -46,13 +67,18 @@ struct FlowC {
 };
 
 // 1-D coordinate tables (FP64), indexed by node index + NG:
-//   x_d(i,j,k) = base[d][i_d] + amp * h[d][i_d] * sn[d][0][i] * sn[d][1][j] * sn[d][2][k]
+//   box: x_d(i,j,k) = base[d][i_d] + amp * h[d][i_d] * sn[d][0][i] * sn[d][1][j] * sn[d][2][k]
+//   cylinder: x = base[0][i], (y, z) = base[1][j] (cth[k], sth[k]), base[1] the radius
 struct Coords {
   const double* base[3];
   const double* h[3];
   const double* sn[3][3];
+  const double* cth;  // cos / sin of the azimuth (cylinder)
+  const double* sth;
   double amp;
+  int cyl;
   __device__ __forceinline__ double x(int d, int i, int j, int k) const {
+    if (cyl) return d == 0 ? base[0][i + NG] : base[1][j + NG] * (d == 1 ? cth[k + NG] : sth[k + NG]);
     int id = d == 0 ? i : (d == 1 ? j : k);
     double b = base[d][id + NG];
     if (amp == 0.0) return b;
@@ -87,12 +113,8 @@ constexpr int DIAG_WORDS = 11;    // per-block diagnostics partial
 // inside that grid: its ghost layers are copies of the neighbouring block's
 // nodes (halo exchange), and its first / last node is updated like any
 // interior node.
-enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2, BC_EXCHANGE = 3 };
-
-__host__ __device__ __forceinline__ int map_index(int idx, int n, int periodic) {
-  if (periodic) { int r = idx % n; return r < 0 ? r + n : r; }
-  return idx < 0 ? 0 : (idx > n - 1 ? n - 1 : idx);
-}
+// BC_AXIS is the centreline face (j = 0) of a cylindrical grid.
+enum { BC_PERIODIC = 0, BC_INFLOW = 1, BC_FARFIELD = 2, BC_EXCHANGE = 3, BC_AXIS = 4 };
 
 // SplitMix64 (Steele, Lea & Flood 2014): first output of a generator whose
 // state is x, written from the published definition.

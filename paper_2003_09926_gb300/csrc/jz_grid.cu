@@ -25,10 +25,21 @@ __device__ double stretch_g(const TabParams& p, double H, double s) {
   return s - (p.stretch_c / H) * (tanh((H * s - p.cluster_r) / p.stretch_w) + tanh((H * s + p.cluster_r) / p.stretch_w));
 }
 
-// coordinate at global index idx along direction d
+// coordinate at global index idx along direction d; on a cylindrical grid
+// direction 1 is the radius r in [0, hi[1]] (the odd clustering function on
+// s = j / (nj - 1), so r(-j) = -r(j)) and direction 2 the azimuth
+// 2 pi (k mod P) / P
 __device__ double base_coord(const TabParams& p, int d, double idx) {
   int n = p.gn[d];
   double lo = p.lo[d], hi = p.hi[d];
+  if (p.cyl && d == 1) {
+    const double s = idx / (n - 1);
+    return p.stretch_c == 0.0 ? hi * s : hi * stretch_g(p, hi, s) / stretch_g(p, hi, 1.0);
+  }
+  if (p.cyl && d == 2) {
+    const int P = p.pn[2], kk = (int)idx;
+    return 2.0 * kPi * (double)(((kk % P) + P) % P) / P;
+  }
   if (p.per[d]) return lo + (hi - lo) * idx / n;
   if (d == 0 || p.stretch_c == 0.0) return lo + (hi - lo) * idx / (n - 1);
   double H = 0.5 * (hi - lo), C = 0.5 * (hi + lo);
@@ -36,14 +47,24 @@ __device__ double base_coord(const TabParams& p, int d, double idx) {
   return C + H * stretch_g(p, H, s) / stretch_g(p, H, 1.0);
 }
 
-// tables layout: for d: base[d] (n_d+4), h[d] (n_d+4); then for d, e: sn[d][e] (n_e+4)
+// tables layout: for d: base[d] (n_d+4), h[d] (n_d+4); then for d, e: sn[d][e] (n_e+4);
+// then cos and sin of the azimuth (n_2+4 each)
 __global__ void k_tables(TabParams p, double* tab) {
   long long off = 0;
   long long base_off[3], h_off[3], sn_off[3][3];
   for (int d = 0; d < 3; ++d) { base_off[d] = off; off += p.n[d] + 2 * NG; h_off[d] = off; off += p.n[d] + 2 * NG; }
   for (int d = 0; d < 3; ++d)
     for (int e = 0; e < 3; ++e) { sn_off[d][e] = off; off += p.n[e] + 2 * NG; }
+  const long long c_off = off, s_off = off + p.n[2] + 2 * NG;
+  off += 2LL * (p.n[2] + 2 * NG);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < off; t += (long long)gridDim.x * blockDim.x) {
+    if (t >= c_off) {  // azimuth tables (used by cylindrical grids)
+      const bool c = t < s_off;
+      const int idx = (int)(t - (c ? c_off : s_off)) - NG + p.off[2];
+      const double th = p.cyl ? base_coord(p, 2, idx) : 0.0;
+      tab[t] = c ? cos(th) : sin(th);
+      continue;
+    }
     // find which table t belongs to
     for (int d = 0; d < 3; ++d) {
       long long len = p.n[d] + 2 * NG;
@@ -100,9 +121,12 @@ __global__ void k_metrics(Layout L, Coords C, MT* __restrict__ M, int a0, int a1
         M[(long long)(3 * kd + md) * L.npad + n] = (MT)(t1 - t2);
       }
     }
+    // the centreline of a cylindrical grid has zero volume in this form:
+    // it takes J of the adjacent radial node
+    const int oj = (C.cyl && j == 0) ? 1 : 0;
     double A[3][3];  // A[m][k] = d x_m / d xi_k
     for (int md = 0; md < 3; ++md)
-      for (int kd = 0; kd < 3; ++kd) A[md][kd] = D(md, kd, 0, 0, 0);
+      for (int kd = 0; kd < 3; ++kd) A[md][kd] = D(md, kd, 0, oj, 0);
     double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
                  A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
     M[9LL * L.npad + n] = (MT)(1.0 / det);
@@ -152,7 +176,8 @@ __global__ void k_fill_ghosts(Layout L, Shell s, T* __restrict__ F, int ncomp) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     shell_node(s, t, i, j, k);
-    int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]), mk = map_index(k, L.n[2], L.per[2]);
+    int mi = i, mj = j, mk = k;
+    L.map_node(mi, mj, mk);
     long long g = L.at(i, j, k), src = L.at(mi, mj, mk);
     for (int c = 0; c < ncomp; ++c) F[(long long)c * L.npad + g] = F[(long long)c * L.npad + src];
   }
@@ -247,15 +272,18 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
 }
 
 // Boundary fill in one pass over the padded nodes outside the updated box:
-// each takes the value of the grid node its index maps to (wrap, or clamp
-// onto the two ghost layers): a copy when that node is updated by the
-// stages, its boundary-condition value (computed here from the interior
-// node it reads) when it is a boundary node.  Only updated nodes are read,
-// so the pass is race-free in one launch, and every node gets the value of
-// a boundary pass followed by a ghost copy.
+// each takes the value of the grid node its index maps to (wrap, clamp onto
+// the two ghost layers, or across the centreline of a cylindrical grid): a
+// copy when that node is updated by the stages, its boundary-condition value
+// (computed here from the interior node it reads, or, on the centreline,
+// from the azimuthal means computed before this pass) when it is a boundary
+// node.  Only updated nodes are read, so the pass is race-free in one
+// launch, and every node gets the value of a boundary pass followed by a
+// ghost copy.
 template <typename ST, typename MT>
 __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
-                                          const FlowC& F, ST* __restrict__ Q, const MT* __restrict__ M) {
+                                          const double* axis, const FlowC& F, ST* __restrict__ Q,
+                                          const MT* __restrict__ M) {
   // one node per thread (four per thread with their loads issued together
   // measured slower: fewer resident threads)
   constexpr int U = 1;
@@ -263,7 +291,7 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
   const int bw = blockDim.x;
   for (int tb = blockIdx.x * bw * U + threadIdx.x; tb < tot; tb += gridDim.x * bw * U) {
     long long dst[U], src[U], nb[U];
-    int kind[U], face[U], inf[U];  // kind: 0 copy, 1 inflow, 2 far field, -1 none
+    int kind[U], face[U], inf[U];  // kind: 0 copy, 1 inflow, 2 far field, 3 centreline, -1 none
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int i, j, k;
@@ -278,8 +306,8 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
           (k < 0 && L.bc[4] == BC_EXCHANGE) || (k >= L.n[2] && L.bc[5] == BC_EXCHANGE))
         continue;
       dst[u] = L.at(i, j, k);
-      const int mi = map_index(i, L.n[0], L.per[0]), mj = map_index(j, L.n[1], L.per[1]);
-      const int mk = map_index(k, L.n[2], L.per[2]);
+      int mi = i, mj = j, mk = k;
+      L.map_node(mi, mj, mk);
       if (mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2]) {
         kind[u] = 0;
         src[u] = L.at(mi, mj, mk);
@@ -302,12 +330,18 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
         inf[u] = mk * L.n[1] + mj;
         continue;
       }
+      if (L.bc[f] == BC_AXIS) {  // azimuthal mean of the adjacent radial line
+        kind[u] = 3;
+        inf[u] = mi;
+        continue;
+      }
       kind[u] = 2;  // far field: nearest updated node, normal at the boundary node
       int ci[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) ci[d] = idx[d] < L.lo[d] ? L.lo[d] : (idx[d] > L.hi[d] ? L.hi[d] : idx[d]);
       src[u] = L.at(ci[0], ci[1], ci[2]);
-      nb[u] = L.at(mi, mj, mk);
+      // on the centreline the face metric vanishes: normal of the adjacent radial node
+      nb[u] = L.at(mi, (L.cyl && mj == 0) ? 1 : mj, mk);
     }
     ST qv[U][5], mv[U][3];
     double uin[U];
@@ -334,6 +368,9 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
         for (int c = 0; c < 5; ++c) v[c] = qv[u][c];
       } else if (kind[u] == 1) {
         to_conserved<ST>((ST)F.gm1, ST(1), (ST)uin[u], ST(0), ST(0), (ST)(1.0 / F.gamma), v);
+      } else if (kind[u] == 3) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c] = (ST)axis[c * L.n[0] + inf[u]];
       } else {
         const ST a = mv[u][0], b = mv[u][1], cc = mv[u][2];
         const ST sgn = (face[u] % 2 == 0) ? ST(-1) : ST(1);
@@ -349,9 +386,31 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
 
 template <typename ST, typename MT>
 __global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constant__ Slabs sl,
-                          const double* __restrict__ inflow, const __grid_constant__ FlowC F, ST* __restrict__ Q,
-                          const MT* __restrict__ M) {
-  fill_slab<ST, MT>(L, sl, blockIdx.y, inflow, F, Q, M);
+                          const double* __restrict__ inflow, const double* __restrict__ axis,
+                          const __grid_constant__ FlowC F, ST* __restrict__ Q, const MT* __restrict__ M) {
+  fill_slab<ST, MT>(L, sl, blockIdx.y, inflow, axis, F, Q, M);
+}
+
+// Centreline of a cylindrical grid (the paper's singularity treatment,
+// Section 3 and Section 4.3): for every axial index i and variable v, the
+// mean of Q_v over the P distinct azimuthal nodes of the radial line j = 1,
+// summed in azimuthal order in FP64 (one thread per (i, v): the sequential
+// order the paper keeps for bitwise reproducibility).
+template <typename ST>
+__device__ __forceinline__ void axis_mean(const Layout& L, const ST* __restrict__ Q, double* __restrict__ axis) {
+  const int n = 5 * L.n[0];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int v = t / L.n[0], i = t - v * L.n[0];
+    const ST* q = Q + (long long)v * L.npad + L.at(i, 1, 0);
+    double s = 0.0;
+    for (int k = 0; k < L.pn[2]; ++k) s += (double)q[(long long)k * L.plane];
+    axis[t] = s / L.pn[2];
+  }
+}
+
+template <typename ST>
+__global__ void k_axis_mean(const __grid_constant__ Layout L, const ST* __restrict__ Q, double* __restrict__ axis) {
+  axis_mean<ST>(L, Q, axis);
 }
 
 // batched versions: grid blockIdx.z of the table, state copy `which`
@@ -359,6 +418,7 @@ struct BcCtx {
   Layout L;
   Slabs fill;
   const double* inflow;
+  double* axis;
   FlowC F;
   void* Q[3];
   const void* M;
@@ -367,7 +427,13 @@ struct BcCtx {
 template <typename ST, typename MT>
 __global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
   const BcCtx& X = ctx[blockIdx.z];
-  fill_slab<ST, MT>(X.L, X.fill, blockIdx.y, X.inflow, X.F, (ST*)X.Q[which], (const MT*)X.M);
+  fill_slab<ST, MT>(X.L, X.fill, blockIdx.y, X.inflow, X.axis, X.F, (ST*)X.Q[which], (const MT*)X.M);
+}
+
+template <typename ST>
+__global__ void k_axis_mean_batch(const BcCtx* __restrict__ ctx, int which) {
+  const BcCtx& X = ctx[blockIdx.z];
+  if (X.L.cyl) axis_mean<ST>(X.L, (const ST*)X.Q[which], X.axis);
 }
 
 // Halo exchange between blocks of one grid (the paper's ghost exchange,
@@ -493,6 +559,7 @@ Shell make_shell(const Layout& L, const int a[3], const int b[3]) {
 cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s) {
   long long len = 0;
   for (int d = 0; d < 3; ++d) len += 2LL * (p.n[d] + 2 * NG) + 3LL * (p.n[d] + 2 * NG);
+  len += 2LL * (p.n[2] + 2 * NG);
   k_tables<<<grid_blocks(len, 256), 256, 0, s>>>(p, tables);
   count_launches(1);
   return cudaGetLastError();
@@ -552,15 +619,23 @@ int slab_blocks(const Slabs& sl) {
 cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
   const Slabs sl = bc_slabs(g.L);
   const dim3 b(slab_blocks(sl), 6);
+  if (g.L.cyl) {
+    const int ab = (5 * g.L.n[0] + 127) / 128;
+    if (g.prec == JZ_P64)
+      k_axis_mean<double><<<ab, 128, 0, s>>>(g.L, (const double*)Q, g.axis);
+    else
+      k_axis_mean<float><<<ab, 128, 0, s>>>(g.L, (const float*)Q, g.axis);
+    count_launches(1);
+  }
   switch (g.prec) {
     case JZ_P64:
-      k_bc_fill<double, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (double*)Q, (const double*)g.M);
+      k_bc_fill<double, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (double*)Q, (const double*)g.M);
       break;
     case JZ_P32_M64:
-      k_bc_fill<float, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (float*)Q, (const double*)g.M);
+      k_bc_fill<float, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const double*)g.M);
       break;
     default:
-      k_bc_fill<float, float><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.F, (float*)Q, (const float*)g.M);
+      k_bc_fill<float, float><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const float*)g.M);
       break;
   }
   count_launches(1);
@@ -575,6 +650,7 @@ void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
   X.L = g.L;
   X.fill = bc_slabs(g.L);
   X.inflow = g.inflow;
+  X.axis = g.axis;
   X.F = g.F;
   X.Q[0] = g.Q0;
   X.Q[1] = g.QA;
@@ -583,9 +659,17 @@ void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
   *blocks = slab_blocks(X.fill);
 }
 
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, cudaStream_t s) {
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, bool cyl, cudaStream_t s) {
   const dim3 b(blocks, 6, n);
   const BcCtx* X = (const BcCtx*)ctx;
+  if (cyl) {  // some grid of the batch is cylindrical: centreline means first
+    const dim3 ab(8, 1, n);
+    if (prec == JZ_P64)
+      k_axis_mean_batch<double><<<ab, 128, 0, s>>>(X, which);
+    else
+      k_axis_mean_batch<float><<<ab, 128, 0, s>>>(X, which);
+    count_launches(1);
+  }
   switch (prec) {
     case JZ_P64: k_bc_fill_batch<double, double><<<b, 256, 0, s>>>(X, which); break;
     case JZ_P32_M64: k_bc_fill_batch<float, double><<<b, 256, 0, s>>>(X, which); break;

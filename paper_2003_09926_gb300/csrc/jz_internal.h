@@ -22,6 +22,7 @@ struct GridDev {
   Scalars* sc;         // device scalars
   double* partial;     // reduction partials: RED_BLOCKS * DIAG_WORDS doubles
   double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
+  double* axis;        // centreline values of a cylindrical grid, [5][ni] FP64 (set per boundary pass)
   FlowC F;
   int kc;              // planes per CTA chunk of the stage kernel
   int goff[3], gn[3];  // global index of local node 0 and global node counts (blocks; else 0 and n)
@@ -41,7 +42,8 @@ struct Shell {
 Shell make_shell(const Layout& L, const int a[3], const int b[3]);
 
 struct TabParams {
-  int n[3], per[3];
+  int n[3], per[3], pn[3];
+  int cyl;
   int off[3], gn[3];  // global index of local node 0, global node counts (a block of a larger grid)
   double lo[3], hi[3];
   double cluster_r, stretch_c, stretch_w, amp;
@@ -63,7 +65,7 @@ cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
 // batched boundary fill over a device table of per-grid contexts
 size_t bc_ctx_bytes();
 void bc_ctx_fill(void* host_dst, const GridDev& g, int* blocks);
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, cudaStream_t s);
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, bool cyl, cudaStream_t s);
 
 // halo exchange between blocks of one grid: one entry per (block, exchange face)
 struct XEntry {

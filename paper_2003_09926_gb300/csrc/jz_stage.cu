@@ -174,8 +174,9 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     if (c.sig_half)  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
       lt[k] = lam[k] + sq[k] * (sq[a] + sq[b]);
     else
-      lt[k] = lam[k] * (R(1) + Fn<R>::powp(Fn<R>::div(lam[a], lam[k]), c.sigma) +
-                        Fn<R>::powp(Fn<R>::div(lam[b], lam[k]), c.sigma));
+      lt[k] = lam[k] > R(0) ? lam[k] * (R(1) + Fn<R>::powp(Fn<R>::div(lam[a], lam[k]), c.sigma) +
+                                        Fn<R>::powp(Fn<R>::div(lam[b], lam[k]), c.sigma))
+                            : R(0);  // zero face metric (a centreline): the limit for sigma < 1
     R pm, pp;
     if (k == 0) { pm = at(sC, V_P, 0, -1); pp = at(sC, V_P, 0, 1); }
     else if (k == 1) { pm = at(sC, V_P, -1, 0); pp = at(sC, V_P, 1, 0); }

@@ -201,8 +201,9 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
     if (c.sig_half)  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
       lt[k] = lam[k] + sq[k] * (sq[a] + sq[b]);
     else
-      lt[k] = lam[k] * (1.f + Fn<float>::powp(Fn<float>::div(lam[a], lam[k]), c.sigma) +
-                        Fn<float>::powp(Fn<float>::div(lam[b], lam[k]), c.sigma));
+      lt[k] = lam[k] > 0.f ? lam[k] * (1.f + Fn<float>::powp(Fn<float>::div(lam[a], lam[k]), c.sigma) +
+                                       Fn<float>::powp(Fn<float>::div(lam[b], lam[k]), c.sigma))
+                           : 0.f;  // zero face metric (a centreline): the limit for sigma < 1
     float pm, pp;
     if (k == 0) { pm = PP[sC + o - 1]; pp = PP[sC + o + 1]; }
     else if (k == 1) { pm = PP[sC + o - RR]; pp = PP[sC + o + RR]; }

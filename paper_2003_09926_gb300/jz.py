@@ -33,7 +33,7 @@ class GridDesc(C.Structure):
     _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int), ("bc", C.c_int * 6),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("cluster_r", C.c_double), ("stretch_c", C.c_double), ("stretch_w", C.c_double),
-                ("map_amp", C.c_double), ("map_seed", C.c_uint64), ("precision", C.c_int)]
+                ("map_amp", C.c_double), ("map_seed", C.c_uint64), ("precision", C.c_int), ("geom", C.c_int)]
 
 
 class FlowParams(C.Structure):
@@ -140,6 +140,7 @@ def make_desc(d: dict) -> GridDesc:
     g.map_amp = d.get("map_amp", 0.0)
     g.map_seed = d.get("map_seed", 0)
     g.precision = d.get("precision", 0)
+    g.geom = d.get("geom", 0)
     return g
 
 

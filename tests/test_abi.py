@@ -72,3 +72,33 @@ def test_null_handles_rejected(L):
     assert L.jz_grid_destroy(None) == jz.JZ_OK
     n = C.c_uint64()
     assert L.jz_launch_count(C.byref(n)) == jz.JZ_OK
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda d: d.update(nk=14), "nk - 1 even"),
+    (lambda d: d.update(map_amp=0.01), "mapping"),
+    (lambda d: d.update(lo=[0.0, 0.5, 0.0]), "lo[1] = 0"),
+    (lambda d: d.update(bc=[W.BC_INFLOW, W.BC_FARFIELD, W.BC_FARFIELD, W.BC_FARFIELD, W.BC_PERIODIC,
+                            W.BC_PERIODIC]), "JZ_BC_AXIS"),
+    (lambda d: d.update(bc=[W.BC_INFLOW, W.BC_FARFIELD, W.BC_AXIS, W.BC_FARFIELD, W.BC_FARFIELD,
+                            W.BC_FARFIELD]), "periodic in k"),
+    (lambda d: d.update(geom=W.GEOM_BOX), "centreline"),
+    (lambda d: d.update(geom=5), "geometry"),
+])
+def test_bad_cylinder_descriptors_rejected(L, mutate, msg):
+    d = W.cyl_grid(16, 8, 13)
+    assert jz.jz_grid_bytes(d) > 0
+    mutate(d)
+    with pytest.raises(jz.JzError) as ei:
+        jz.jz_grid_bytes(d)
+    assert ei.value.code == jz.JZ_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_cylinder_blocks_split_in_i_only(L):
+    d = W.cyl_grid(40, 8, 13)
+    assert jz.jz_block_bytes(d, (0, 0, 0), (19, 7, 12)) > 0
+    for o0, o1 in (((0, 0, 0), (39, 3, 12)), ((0, 0, 0), (39, 7, 5))):
+        with pytest.raises(jz.JzError) as ei:
+            jz.jz_block_bytes(d, o0, o1)
+        assert ei.value.code == jz.JZ_EINVAL
