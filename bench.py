@@ -168,10 +168,15 @@ def stage_traffic(prec: int):
 
 
 def interior_points(grid: dict) -> int:
+    """Nodes the Runge-Kutta stages update (a cylinder's last azimuthal
+    plane repeats its first and is not counted)."""
     n = 1
     for a, key in enumerate(("ni", "nj", "nk")):
         per = grid["bc"][2 * a] == 0
-        n *= grid[key] if per else grid[key] - 2
+        if per:
+            n *= grid[key] - 1 if (a == 2 and grid.get("geom", 0) == 1) else grid[key]
+        else:
+            n *= grid[key] - 2
     return n
 
 
@@ -309,6 +314,26 @@ def bench_batched(jz, torch, W, local: int, steps: int, steps64: int, cfl: float
             "speedup": v32 / v64}
 
 
+def bench_cylinder(jz, torch, W, local: int, steps: int, steps64: int, cfl: float = 0.5):
+    """The paper's own geometry at its mesh 6 (Tab. mesh: 256 x 128 x 361,
+    about 11.8 M points): the cylindrical jet grid with the centreline
+    treatment, FP32 (vector-record kernel) and plain FP64, graph-replayed
+    steps timed with CUDA events."""
+    out = {"workload": "paper mesh 6: cylinder 256x128x361 (axial x radial x azimuthal), jet, CFL 0.5"}
+    for prec, n in ((W.P32, steps), (W.P64, steps64)):
+        grid = W.cyl_grid(256, 128, 361, precision=prec)
+        stream = torch.cuda.Stream(device=local)
+        g = jz.Grid(grid, stream=stream, device=local).init(W.jet_flow(), 1)
+        ms, launches = time_steps(jz, torch, g, n, cfl, 1)
+        pts = interior_points(grid)
+        d = g.diagnostics()
+        out[W.PRECISION_NAMES[prec]] = {"value": pts * 5 * n / (ms / 1e3) / 1e6, "unit": UNIT, "steps": n,
+                                        "ms_per_step": ms / n, "points_updated": pts,
+                                        "launches_per_step": launches / n, "finite": d["nonfinite"] == 0}
+        g.close()
+    return out
+
+
 def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6):
     """Continuous batching on a bounded serving trace: log-uniform 1e5..2e6
     points per case, 50..500 steps, Poisson arrivals at 70% of the measured
@@ -374,6 +399,7 @@ def main(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 variant (default steps/10)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-grid batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-cylinder", action="store_true", help="skip the cylindrical-grid measurement")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -400,7 +426,7 @@ def main(argv=None):
     clocks = None
     prof = prof64 = None
     launches = 0
-    for prec in (head, W.P32_M64, W.P64):
+    for prec in (head, W.P32_M64, W.P32_S64, W.P64):
         g = jz.Grid(dict(grid, precision=prec), device=local).init(cfg["flow"], cfg["seed"] + rank)
         steps = args.steps if prec != W.P64 else (args.fp64_steps or max(3, args.steps // 10))
         for _ in range(args.warmup):
@@ -428,7 +454,7 @@ def main(argv=None):
     ref.close()
     del ref
     errors = {}
-    for prec in (W.P32_M64, W.P32):
+    for prec in (W.P32_M64, W.P32, W.P32_S64):
         g = jz.Grid(dict(grid, precision=prec), device=local).init(cfg["flow"], cfg["seed"])
         g.nsteps(err_steps, cfl=cfg["cfl"])
         Q = g.download()
@@ -520,6 +546,8 @@ def main(argv=None):
     if not args.no_serving:
         cap = line["batched"]["fp32_batched"]["value"] if "batched" in line else results[head]["value"]
         line["serving"] = bench_serving(jz, torch, W, local, cap)
+    if not args.no_cylinder:
+        line["cylinder"] = bench_cylinder(jz, torch, W, local, steps=max(10, args.steps // 4), steps64=2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_baseline(cfg)
     if rank == 0:

@@ -64,6 +64,10 @@ extern "C" {
 #define JZ_P64 0     /* FP64 state and fluxes, FP64 metrics                   */
 #define JZ_P32_M64 1 /* FP32 state and fluxes, FP64-stored metrics             */
 #define JZ_P32 2     /* FP32 state and fluxes, FP64-generated FP32 metrics     */
+#define JZ_P32_S64 3 /* FP32 fluxes and stage states, FP64 state between steps,
+                      * FP32 metrics: the update adds the FP32 increment to an
+                      * FP64 copy of Q^n at the updated nodes, so the state does
+                      * not lose the increments smaller than its FP32 spacing */
 
 /* initial conditions */
 #define JZ_IC_JET 0       /* top-hat jet column plus seeded velocity noise     */

@@ -57,7 +57,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Carve {
   Layout L;
   size_t es, ms;  // state / metric element sizes
-  size_t off_sc, off_partial, off_tab, off_inflow, off_axis, off_q0, off_qa, off_qb, off_m, total;
+  size_t off_sc, off_partial, off_tab, off_inflow, off_axis, off_q0, off_qa, off_qb, off_m, off_q0d, total;
   size_t tab_len;
 };
 
@@ -78,7 +78,7 @@ static int validate(const jz_grid_desc* d) {
   }
   for (int f = 1; f < 6; ++f)
     if (d->bc[f] == JZ_BC_INFLOW) return fail(JZ_EINVAL, "the inflow condition is supported on the x- face only");
-  if (d->precision != JZ_P64 && d->precision != JZ_P32_M64 && d->precision != JZ_P32)
+  if (d->precision != JZ_P64 && d->precision != JZ_P32_M64 && d->precision != JZ_P32 && d->precision != JZ_P32_S64)
     return fail(JZ_EINVAL, "bad precision mode %d", d->precision);
   if (d->stretch_c != 0.0 && !(d->stretch_w > 0.0)) return fail(JZ_EINVAL, "stretch_w must be > 0");
   if (!std::isfinite(d->map_amp) || !std::isfinite(d->stretch_c) || !std::isfinite(d->cluster_r))
@@ -144,7 +144,7 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
   L.plane = (long long)L.pitch * (L.n[1] + 2 * NG);
   L.npad = L.plane * (L.n[2] + 2 * NG);
   c.es = d->precision == JZ_P64 ? 8 : 4;
-  c.ms = d->precision == JZ_P32 ? 4 : 8;
+  c.ms = (d->precision == JZ_P32 || d->precision == JZ_P32_S64) ? 4 : 8;
   c.tab_len = 0;
   for (int a = 0; a < 3; ++a) c.tab_len += 5 * (size_t)(L.n[a] + 2 * NG);
   c.tab_len += 2 * (size_t)(L.n[2] + 2 * NG);  // azimuth cos / sin
@@ -159,6 +159,8 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
   c.off_qa = off; off += qbytes;
   c.off_qb = off; off += qbytes;
   c.off_m = off; off += align256(10 * (size_t)L.npad * c.ms);
+  c.off_q0d = off;  // FP64 state of a JZ_P32_S64 grid
+  if (d->precision == JZ_P32_S64) off += align256(5 * (size_t)L.npad * 8);
   c.total = off;
   return c;
 }
@@ -397,6 +399,7 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
   d.QA = g->base + cv.off_qa;
   d.QB = g->base + cv.off_qb;
   d.M = g->base + cv.off_m;
+  d.Q0d = d.prec == JZ_P32_S64 ? (double*)(g->base + cv.off_q0d) : nullptr;
   d.sc = (Scalars*)(g->base + cv.off_sc);
   d.partial = (double*)(g->base + cv.off_partial);
   d.inflow = (double*)(g->base + cv.off_inflow);
@@ -444,7 +447,7 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
       tp.m[3 * a + e] = 1 + (int)(splitmix64(desc->map_seed ^ (2 * c)) % 3ULL);
       tp.th[3 * a + e] = 2.0 * 3.14159265358979323846 * unit53(splitmix64(desc->map_seed ^ (2 * c + 1)));
     }
-  const bool st64 = d.prec == JZ_P64, mt64 = d.prec != JZ_P32;
+  const bool st64 = d.prec == JZ_P64, mt64 = d.prec == JZ_P64 || d.prec == JZ_P32_M64;
   if ((rc = make_plane_map(&d.tmQ[0], d.Q0, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmQ[1], d.QA, st64, cv.L, 5, d.prec)) ||
       (rc = make_plane_map(&d.tmQ[2], d.QB, st64, cv.L, 5, d.prec)) ||

@@ -486,8 +486,8 @@ __global__ void k_inflow(Layout L, Coords C, FlowC F, double* __restrict__ inflo
 // of local node 0, gn: global node counts), so a block of a larger grid gets
 // the values of the same nodes of the whole grid.
 template <typename ST>
-__global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restrict__ Q, int go0, int go1, int go2,
-                       int gn0, int gn1) {
+__global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restrict__ Q, double* __restrict__ Q0d,
+                       int go0, int go1, int go2, int gn0, int gn1) {
   long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
     int i = (int)(t % L.n[0]);
@@ -507,11 +507,14 @@ __global__ void k_init(Layout L, Coords C, FlowC F, uint64_t seed, ST* __restric
     to_conserved<double>(F.gm1, 1.0, u[0], u[1], u[2], 1.0 / F.gamma, q);
     long long n = L.at(i, j, k);
     for (int v = 0; v < 5; ++v) Q[(long long)v * L.npad + n] = (ST)q[v];
+    if (Q0d)
+      for (int v = 0; v < 5; ++v) Q0d[(long long)v * L.npad + n] = q[v];
   }
 }
 
+// the state Q (rounded to ST) and, for a JZ_P32_S64 grid, its FP64 copy Q0d
 template <typename ST>
-__global__ void k_unpack(Layout L, const double* __restrict__ dense, ST* __restrict__ Q) {
+__global__ void k_unpack(Layout L, const double* __restrict__ dense, ST* __restrict__ Q, double* __restrict__ Q0d) {
   long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * N; t += (long long)gridDim.x * blockDim.x) {
     int v = (int)(t / N);
@@ -519,12 +522,17 @@ __global__ void k_unpack(Layout L, const double* __restrict__ dense, ST* __restr
     int i = (int)(r % L.n[0]);
     int j = (int)((r / L.n[0]) % L.n[1]);
     int k = (int)(r / ((long long)L.n[0] * L.n[1]));
-    Q[(long long)v * L.npad + L.at(i, j, k)] = (ST)dense[t];
+    const long long e = (long long)v * L.npad + L.at(i, j, k);
+    Q[e] = (ST)dense[t];
+    if (Q0d) Q0d[e] = dense[t];
   }
 }
 
+// Q0d (FP64 state of a JZ_P32_S64 grid, else null) supplies the updated
+// nodes (and the superposed azimuthal plane of a cylinder, a copy of plane 0);
+// boundary nodes come from the state Q.
 template <typename ST>
-__global__ void k_pack(Layout L, const ST* __restrict__ Q, double* __restrict__ dense) {
+__global__ void k_pack(Layout L, const ST* __restrict__ Q, const double* __restrict__ Q0d, double* __restrict__ dense) {
   long long N = (long long)L.n[0] * L.n[1] * L.n[2];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * N; t += (long long)gridDim.x * blockDim.x) {
     int v = (int)(t / N);
@@ -532,7 +540,12 @@ __global__ void k_pack(Layout L, const ST* __restrict__ Q, double* __restrict__ 
     int i = (int)(r % L.n[0]);
     int j = (int)((r / L.n[0]) % L.n[1]);
     int k = (int)(r / ((long long)L.n[0] * L.n[1]));
-    dense[t] = (double)Q[(long long)v * L.npad + L.at(i, j, k)];
+    int mi = i, mj = j, mk = k;
+    L.map_node(mi, mj, mk);
+    if (Q0d && mi >= L.lo[0] && mi <= L.hi[0] && mj >= L.lo[1] && mj <= L.hi[1] && mk >= L.lo[2] && mk <= L.hi[2])
+      dense[t] = Q0d[(long long)v * L.npad + L.at(mi, mj, mk)];
+    else
+      dense[t] = (double)Q[(long long)v * L.npad + L.at(i, j, k)];
   }
 }
 
@@ -574,7 +587,7 @@ cudaError_t launch_metrics(const GridDev& g, cudaStream_t s) {
   }
   const long long N = (long long)(b[0] - a[0] + 1) * (b[1] - a[1] + 1) * (b[2] - a[2] + 1);
   Shell sh = make_shell(g.L, a, b);  // the remaining ghost nodes copy the node their index maps to
-  if (g.prec == JZ_P32) {
+  if (g.prec == JZ_P32 || g.prec == JZ_P32_S64) {
     k_metrics<float><<<grid_blocks(N, 128), 128, 0, s>>>(g.L, g.C, (float*)g.M, a[0], a[1], a[2], b[0], b[1], b[2]);
     k_fill_ghosts<float><<<grid_blocks(sh.total(), 256), 256, 0, s>>>(g.L, sh, (float*)g.M, 10);
   } else {
@@ -590,11 +603,11 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
   k_inflow<<<grid_blocks((long long)g.L.n[1] * g.L.n[2], 256), 256, 0, s>>>(g.L, g.C, g.F, g.inflow);
   count_launches(1);
   if (g.prec == JZ_P64)
-    k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0, g.goff[0], g.goff[1],
-                                                       g.goff[2], g.gn[0], g.gn[1]);
+    k_init<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (double*)g.Q0, nullptr, g.goff[0],
+                                                       g.goff[1], g.goff[2], g.gn[0], g.gn[1]);
   else
-    k_init<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (float*)g.Q0, g.goff[0], g.goff[1],
-                                                      g.goff[2], g.gn[0], g.gn[1]);
+    k_init<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, g.C, g.F, seed, (float*)g.Q0, g.Q0d, g.goff[0],
+                                                      g.goff[1], g.goff[2], g.gn[0], g.gn[1]);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -682,9 +695,9 @@ cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int wh
 cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s) {
   long long N = 5LL * g.L.n[0] * g.L.n[1] * g.L.n[2];
   if (g.prec == JZ_P64)
-    k_unpack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (double*)g.Q0);
+    k_unpack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (double*)g.Q0, nullptr);
   else
-    k_unpack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (float*)g.Q0);
+    k_unpack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (float*)g.Q0, g.Q0d);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -692,9 +705,9 @@ cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s)
 cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s) {
   long long N = 5LL * g.L.n[0] * g.L.n[1] * g.L.n[2];
   if (g.prec == JZ_P64)
-    k_pack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.Q0, dense);
+    k_pack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.Q0, nullptr, dense);
   else
-    k_pack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.Q0, dense);
+    k_pack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.Q0, g.Q0d, dense);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -15,6 +15,7 @@ struct GridDev {
   Layout L;
   int prec;            // JZ_P64, JZ_P32_M64, JZ_P32
   void* Q0;            // Q^n, then Q^(5) in place
+  double* Q0d;         // JZ_P32_S64: the FP64 state Q^n at the updated nodes (else null)
   void* QA;            // Q^(1), Q^(3)
   void* QB;            // Q^(2), Q^(4)
   void* M;             // metrics: S^k_m at field 3k+m, J at field 9

@@ -221,7 +221,11 @@ __device__ __forceinline__ void face5(const R* ring, const int so[4], const int 
 // One work item: the tile (bx, by) and k-chunk bz of grid X for stage st.
 // ph[] counts completed phases of the three mbarriers (identical in every
 // thread); issued[] / waited[] are kept by thread 0 for the timeout path.
-template <typename R, typename MT, int TI, int TJ>
+// S64: the state between time steps is FP64 (X.Q0d, interior nodes): the
+// update adds the FP32 increment to it in FP64, stages 1-4 round their
+// output to FP32 (it feeds only the FP32 flux evaluation), and stage 5 writes
+// both the FP64 state and its FP32 copy (the next step's flux input).
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const StageSel& st, int bx, int by, int bz,
                                            unsigned char* smem, uint32_t ph[3], int issued[3], int waited[3],
                                            bool& failed) {
@@ -457,11 +461,17 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
   // ---- march in k
   for (int t = t0; t < t1 && !failed; ++t) {
     R q0[5];
+    double q0d[5];
     long long n = 0;
     if (own) {
       n = L.at(gi, gj, t);
+      if constexpr (S64) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) q0[v] = X.Q[0][v * npad + n];
+        for (int v = 0; v < 5; ++v) q0d[v] = X.Q0d[v * npad + n];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q0[v] = X.Q[0][v * npad + n];
+      }
     }
     // the barrier inside fetch_plane also orders the previous iteration's
     // reads of ring slot t-2 and of the face buffers before they are rewritten
@@ -476,8 +486,17 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
       R hk[5];
       kface(t, G3c, G3n, lt3c, lt3n, nu3c, nu3n, hk);
       if (own) {
+        if constexpr (S64) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
+          for (int v = 0; v < 5; ++v) {
+            const double qn = q0d[v] - (double)(adt * Jc * (Rc[v] + (hk[v] - hprev[v])));
+            Qo[v * npad + n] = (R)qn;
+            if (st.qout == 0) X.Q0d[v * npad + n] = qn;
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Qo[v * npad + n] = q0[v] - adt * Jc * (Rc[v] + (hk[v] - hprev[v]));
+        }
       }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -494,7 +513,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
 }
 
 // One grid: one CTA per (tile, k-chunk).
-template <typename R, typename MT, int TI, int TJ>
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage(const __grid_constant__ StageCtx<R, MT> X, const StageSel st) {
   using C = Cfg<R, MT, TI, TJ>;
@@ -504,13 +523,13 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
   uint32_t ph[3] = {0, 0, 0};
   int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};
   bool failed = false;
-  stage_item<R, MT, TI, TJ>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
+  stage_item<R, MT, TI, TJ, S64>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
   if (failed) drain_after_timeout(bar, X.err, issued, waited);
 }
 
 // Many grids: persistent CTAs (one per SM) take work items (grid, tile,
 // k-chunk) from a device queue, largest first.
-template <typename R, typename MT, int TI, int TJ>
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage_batch(const StageCtx<R, MT>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
                   unsigned int* queue, const StageSel st) {
@@ -531,7 +550,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
     if (it >= nitems) break;
     const int4 w = items[it];
     gsel = w.x;
-    stage_item<R, MT, TI, TJ>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
+    stage_item<R, MT, TI, TJ, S64>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
     if (failed) break;
   }
   if (failed) drain_after_timeout(bar, ctx[gsel].err, issued, waited);
@@ -544,12 +563,12 @@ constexpr int TI32 = 32, TJ32 = 16;  // P32: 608 threads, 191 KB: one CTA per SM
 constexpr int TIM = 32, TJM = 16;    // P32_M64: 608 threads, 220 KB (FP64 metric staging): one CTA per SM
 constexpr int TI64 = 16, TJ64 = 16;  // FP64: 320 threads, 207 KB
 
-template <typename R, typename MT, int TI, int TJ>
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t configure_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Cfg<R, MT, TI, TJ>::BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<R, MT, TI, TJ>::BYTES);
 }
 
@@ -566,6 +585,7 @@ void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
   X.Q[0] = (R*)g.Q0;
   X.Q[1] = (R*)g.QA;
   X.Q[2] = (R*)g.QB;
+  X.Q0d = (double*)g.Q0d;
   X.sc = g.sc;
   X.err = &g.sc->err;
   X.F = g.F;
@@ -573,7 +593,7 @@ void fill_ctx(StageCtx<R, MT>& X, const GridDev& g) {
   X.kc = g.kc;
 }
 
-template <typename R, typename MT, int TI, int TJ>
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t launch_one(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s) {
   using Cf = Cfg<R, MT, TI, TJ>;
   StageCtx<R, MT> X;
@@ -581,12 +601,12 @@ cudaError_t launch_one(const GridDev& g, int stage, int qsel, int qout, cudaStre
   const StageSel st{kRkAlpha[stage], qsel, qout};
   const int nz = g.L.hi[2] - g.L.lo[2] + 1;
   dim3 grid((g.L.hi[0] + TI) / TI, (g.L.hi[1] + TJ) / TJ, (nz + g.kc - 1) / g.kc);
-  k_stage<R, MT, TI, TJ><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
+  k_stage<R, MT, TI, TJ, S64><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <typename R, typename MT, int TI, int TJ>
+template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue, int stage, int qsel,
                          int qout, cudaStream_t s) {
   using Cf = Cfg<R, MT, TI, TJ>;
@@ -594,7 +614,7 @@ cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigne
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const int ctas = nitems < 152 * Cf::MINB ? nitems : 152 * Cf::MINB;
-  k_stage_batch<R, MT, TI, TJ><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
+  k_stage_batch<R, MT, TI, TJ, S64><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -620,6 +640,7 @@ cudaError_t stage_configure() {
   if ((e = configure_one<double, double, TI64, TJ64>()) != cudaSuccess) return e;
   if ((e = configure_one<float, double, TIM, TJM>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32>()) != cudaSuccess) return e;
+  if ((e = configure_one<float, float, TI32, TJ32, true>()) != cudaSuccess) return e;
   if ((e = stage_v_configure()) != cudaSuccess) return e;
   return cudaSuccess;
 }
@@ -628,6 +649,7 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
   switch (g.prec) {
     case JZ_P64: return launch_one<double, double, TI64, TJ64>(g, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_one<float, double, TIM, TJM>(g, stage, qsel, qout, s);
+    case JZ_P32_S64: return launch_one<float, float, TI32, TJ32, true>(g, stage, qsel, qout, s);
     default:
       if (g.variant == 2) {
         StageCtx<float, float> X;
@@ -661,6 +683,8 @@ cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int
   switch (prec) {
     case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, s);
+    case JZ_P32_S64:
+      return launch_batch<float, float, TI32, TJ32, true>(ctx, items, nitems, queue, stage, qsel, qout, s);
     default: return launch_batch<float, float, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
   }
 }

@@ -177,6 +177,7 @@ struct alignas(128) StageCtx {
   CUtensorMap tmQ0u;   // Q0, box of the tile rows (FP32 record kernel's update)
   Layout L;
   R* Q[3];             // Q0, QA, QB
+  double* Q0d;         // FP64 state between steps (JZ_P32_S64; else null)
   const Scalars* sc;
   int* err;            // sticky error flag (bounded-wait timeout)
   FlowC F;

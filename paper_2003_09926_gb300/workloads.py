@@ -15,10 +15,10 @@ import numpy as np
 
 BC_PERIODIC, BC_INFLOW, BC_FARFIELD, BC_AXIS = 0, 1, 2, 4
 GEOM_BOX, GEOM_CYLINDER = 0, 1
-P64, P32_M64, P32 = 0, 1, 2
+P64, P32_M64, P32, P32_S64 = 0, 1, 2, 3
 IC_JET, IC_QUIESCENT = 0, 1
 SGS_SMAGORINSKY, SGS_VREMAN = 0, 1
-PRECISION_NAMES = {P64: "P64", P32_M64: "P32_M64", P32: "P32"}
+PRECISION_NAMES = {P64: "P64", P32_M64: "P32_M64", P32: "P32", P32_S64: "P32_S64"}
 
 JET_BC = [BC_INFLOW, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD]
 ALL_PERIODIC = [BC_PERIODIC] * 6
