@@ -334,6 +334,26 @@ def bench_cylinder(jz, torch, W, local: int, steps: int, steps64: int, cfl: floa
     return out
 
 
+def bench_billion(jz, torch, W, local: int, steps: int, cfl: float = 0.5):
+    """The paper's largest mesh size (Tab. mesh: about 1e9 points) on one GPU:
+    c2, 1024 x 1024 x 960 mapped jet in FP32 (state, fluxes and stored
+    metrics; about 104 GB of HBM), graph-replayed steps."""
+    cfg = W.config2()
+    grid = cfg["grid"]
+    stream = torch.cuda.Stream(device=local)
+    g = jz.Grid(grid, stream=stream, device=local).init(cfg["flow"], cfg["seed"])
+    ms, launches = time_steps(jz, torch, g, steps, cfl, 1)
+    pts = interior_points(grid)
+    d = g.diagnostics()
+    out = {"workload": "c2: 1024x1024x960 mapped jet (1.007e9 points), P32", "value": pts * 5 * steps / (ms / 1e3) / 1e6,
+           "unit": UNIT, "steps": steps, "ms_per_step": ms / steps, "points_updated": pts,
+           "device_bytes": g.nbytes, "launches_per_step": launches / steps, "finite": d["nonfinite"] == 0}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6):
     """Continuous batching on a bounded serving trace: log-uniform 1e5..2e6
     points per case, 50..500 steps, Poisson arrivals at 70% of the measured
@@ -400,6 +420,7 @@ def main(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-grid batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-cylinder", action="store_true", help="skip the cylindrical-grid measurement")
+    ap.add_argument("--no-billion", action="store_true", help="skip the 1e9-point measurement")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -548,6 +569,8 @@ def main(argv=None):
         line["serving"] = bench_serving(jz, torch, W, local, cap)
     if not args.no_cylinder:
         line["cylinder"] = bench_cylinder(jz, torch, W, local, steps=max(10, args.steps // 4), steps64=2)
+    if not args.no_billion and world == 1:
+        line["billion"] = bench_billion(jz, torch, W, local, steps=max(3, args.steps // 40))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_baseline(cfg)
     if rank == 0:
