@@ -153,7 +153,8 @@ typedef struct jz_batch jz_batch;
 int jz_last_error(char* buf, size_t len);
 
 /* Device bytes a grid with this descriptor needs (state x3, metrics,
- * coordinate tables, reduction scratch).  Pure arithmetic: used for
+ * coordinate tables, reduction scratch; the FP64 state copy of a JZ_P32_S64
+ * grid; the centreline means of a cylinder).  Pure arithmetic: used for
  * HBM-budget admission.  JZ_EINVAL on a bad descriptor. */
 int jz_grid_bytes(const jz_grid_desc* desc, size_t* bytes);
 
@@ -208,19 +209,21 @@ int jz_diagnostics(jz_grid* g, jz_diag* out);
 
 /* Copy the state to host memory: n = 5*ni*nj*nk doubles, layout [v][k][j][i]
  * (conserved rho, rho u, rho v, rho w, e), ghosts excluded; FP32 states are
- * widened.  Synchronises the stream. */
+ * widened (JZ_P32_S64: the updated nodes come from the FP64 state, boundary
+ * nodes from the FP32 one).  Synchronises the stream. */
 int jz_state_download(jz_grid* g, double* host, size_t n);
 
 /* Replace the state from host memory (layout as jz_state_download; values
  * at boundary nodes are overwritten by the boundary conditions, which are
- * applied after the upload).  Requires jz_state_init to have set the flow
- * parameters.  Synchronises the stream (host buffer may be reused on return). */
+ * applied after the upload; a JZ_P32_S64 grid keeps the FP64 values of its
+ * updated nodes).  Requires jz_state_init to have set the flow parameters.
+ * Synchronises the stream (host buffer may be reused on return). */
 int jz_state_upload(jz_grid* g, const double* host, size_t n);
 
 /* Batched execution of many grids: per stage, one persistent launch whose
  * CTAs take (grid, tile, k-chunk) work items from a device queue, largest
- * first, plus one batched boundary fill; per step one batched time-step
- * reduction.  The batch borrows the grids (one precision mode, flow
+ * first, plus one batched boundary fill (preceded by the centreline means
+ * when a grid is cylindrical); per step one batched time-step reduction.  The batch borrows the grids (one precision mode, flow
  * parameters set; they must outlive the batch and keep the k-chunk length
  * they had at jz_batch_create) and a caller-owned, 256-byte aligned device
  * buffer of jz_batch_bytes bytes for its tables; work goes to `stream`
@@ -320,8 +323,9 @@ int jz_set_tiling(jz_grid* g, int kc);
  * 0 is the scalar kernel (one shared-memory value per load, four barriers
  * per plane).  Both evaluate the same formulas; results agree to FP32
  * rounding.  Measured on the 256x192x192 mapped jet: 0.41 ms (2) and 0.55 ms
- * (0) per stage.  JZ_EINVAL for other precisions or variants.  A batch uses
- * its first grid's variant. */
+ * (0) per stage.  Grids of the other precision modes (JZ_P64, JZ_P32_M64,
+ * JZ_P32_S64) run the scalar kernel only: JZ_EINVAL for variant 2 there, and
+ * for other variants.  A batch uses its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
 /* --- diagnostics without device allocation --------------------------------

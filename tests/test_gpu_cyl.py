@@ -134,3 +134,42 @@ def test_cylinder_descriptor_checks(jz):
     for d in bad:
         with pytest.raises(jz.JzError):
             jz.Grid(d)
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (5, 4, 9)])
+def test_smallest_cylinders_match_oracle(jz, orc, shape):
+    """The smallest cylinders the descriptor allows (nj = 4: one radial line
+    between the centreline and the far field; nk = 5: four azimuthal
+    intervals)."""
+    grid = W.cyl_grid(*shape, length=2.0, radius=1.5)
+    flow = W.jet_flow(re=5e3)
+    g = jz.Grid(grid).init(flow, 1)
+    o = orc.Oracle(grid, flow)
+    Q = o.init(1)
+    g.nsteps(4, cfl=0.5)
+    o.run(Q, 4, cfl=0.5)
+    got = g.download()
+    assert rel_err(got, o.inner(Q)) <= 1e-10
+    invariants(got)
+
+
+def test_cylinder_with_vreman_and_fp64_state(jz, orc):
+    """The options combine: Vreman eddy viscosity on the cylinder in FP64
+    (against the oracle) and with the FP64-state FP32 mode (FP32 bounds)."""
+    grid = W.cyl_grid(30, 12, 25)
+    flow = W.jet_flow(re=5e3, sgs=W.SGS_VREMAN)
+    o = orc.Oracle(grid, flow)
+    Q = o.init(6)
+    o.run(Q, 6, cfl=0.5)
+    ref = o.inner(Q)
+    g = jz.Grid(grid).init(flow, 6)
+    g.nsteps(6, cfl=0.5)
+    assert rel_err(g.download(), ref) <= 1e-10
+    g32 = jz.Grid(dict(grid, precision=W.P32_S64)).init(flow, 6)
+    g32.nsteps(6, cfl=0.5)
+    got = g32.download()
+    invariants(got)
+    sel = (slice(None), slice(0, -3), slice(3, -3))
+    for v in range(5):
+        e = np.abs(got[v][sel] - ref[v][sel]).max() / np.abs(ref[v]).max()
+        assert e <= (2e-3 if v in (2, 3) else 5e-5), (v, e)
