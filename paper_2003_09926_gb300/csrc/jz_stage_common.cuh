@@ -97,10 +97,13 @@ template <> struct Fn<double> {
 //   Vreman (2004): c Delta^2 sqrt(B / (g_am g_am)), c = 2.5 C_s^2, with
 //     b_ab = sum_m g[a][m] g[b][m] and B = b00 b11 - b01^2 + b00 b22 - b02^2
 //     + b11 b22 - b12^2 (the sum of b's principal 2x2 minors, >= 0; clamped at
-//     0 against rounding); 0 where all gradients vanish.
+//     0 against rounding); 0 where all gradients vanish.  B <= (g_am g_am)^2/3,
+//     so the model tends to 0 with the gradients: below the smallest normal
+//     number (where the FP32 reciprocal flushes to zero) it is taken as 0.
 template <typename R>
 __device__ __forceinline__ R eddy_nu(const KConst<R>& c, const R g[4][3], R Jn) {
   if (c.vreman) {
+    const R tiny = sizeof(R) == 4 ? R(1.17549435e-38f) : R(2.2250738585072014e-308);
     R b[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -109,7 +112,7 @@ __device__ __forceinline__ R eddy_nu(const KConst<R>& c, const R g[4][3], R Jn) 
     const R aa = b[0][0] + b[1][1] + b[2][2];
     const R B = b[0][0] * b[1][1] - b[0][1] * b[0][1] + b[0][0] * b[2][2] - b[0][2] * b[0][2] +
                 b[1][1] * b[2][2] - b[1][2] * b[1][2];
-    if (!(aa > R(0))) return R(0);
+    if (!(aa > tiny)) return R(0);
     return R(2.5) * c.cs2 * Fn<R>::jm23(Jn) * Fn<R>::sqrt_(Fn<R>::div(rmax(B, R(0)), aa));
   }
   const R s12 = R(0.5) * (g[0][1] + g[1][0]), s13 = R(0.5) * (g[0][2] + g[2][0]);
