@@ -364,12 +364,16 @@ def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, bas
     work = np.mean([interior_points(r["grid"]) * 5 * r["steps"] for r in cfg["requests"]])
     rate = 0.7 * capacity * 1e6 / work
     trace = serve.poisson_trace(cfg, rate)
-    srv = serve.Server(150 * 10**9, slice_steps=10, device=local)
+    fill = 4 * 10**6
+    srv = serve.Server(150 * 10**9, slice_steps=10, device=local, fill_points=fill)
     res = srv.run(trace)
     out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..2e6 points, 50..500 steps, seed 4",
            "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10,
-           "fp32_continuous_batching": serve.summarize(res), "peak_resident_bytes": srv.peak_bytes,
-           "slices": srv.slices}
+           "fp32_continuous_batching": dict(serve.summarize(res), fill_points=fill,
+                                            policy="oldest cases first until they hold fill_points points"),
+           "peak_resident_bytes": srv.peak_bytes, "slices": srv.slices}
+    srv_all = serve.Server(150 * 10**9, slice_steps=10, device=local)
+    out["fp32_batching_all_resident"] = serve.summarize(srv_all.run(trace))
     out["fp32_one_at_a_time"] = serve.summarize(serve.serve_one_at_a_time(trace, W.P32, device=local))
     out["fp64_one_at_a_time_first_cases"] = dict(
         serve.summarize(serve.serve_one_at_a_time(trace[:base64_n], W.P64, device=local)), cases=base64_n)

@@ -3,8 +3,11 @@
 Requests (a grid, flow parameters, a seed, a step count and an arrival time)
 are admitted in arrival order while their device footprint (``jz_grid_bytes``)
 fits an HBM budget; admitted cases stay resident on the device and advance
-together in time slices, each slice one batched launch sequence over every
-resident grid (``jz_batch_nsteps``).  Finished cases are retired at slice
+together in time slices, each slice one batched launch sequence
+(``jz_batch_nsteps``) over the resident grids it selects: all of them, or
+(``fill_points``) the oldest ones until they hold enough points to fill the
+GPU, so that a case is not slowed down by later arrivals once the device is
+busy (first come, first served, with the spare capacity shared).  Finished cases are retired at slice
 boundaries -- their diagnostics (and optionally their state) are read back
 and their memory returned -- so cases that arrive while others run are
 admitted as soon as memory frees up and their work overlaps on the device.
@@ -58,9 +61,24 @@ def updated_points(grid: dict) -> int:
     return n
 
 
+def select_cases(resident: list[dict], fill_points: int | None) -> list[dict]:
+    """The resident cases one slice advances: every case when fill_points is
+    None, else the oldest (arrival, then id) until their updated points reach
+    fill_points."""
+    if fill_points is None:
+        return list(resident)
+    chosen, pts = [], 0
+    for c in sorted(resident, key=lambda c: (c["req"].arrival, c["req"].rid)):
+        chosen.append(c)
+        pts += updated_points(c["req"].grid)
+        if pts >= fill_points:
+            break
+    return chosen
+
+
 class Server:
     def __init__(self, budget_bytes: int, slice_steps: int = 10, cfl: float = 0.5, device: int = 0,
-                 keep_state: bool = False, kc_for=None):
+                 keep_state: bool = False, kc_for=None, fill_points: int | None = None):
         import torch  # device memory and the stream only
         self.torch = torch
         self.budget = int(budget_bytes)
@@ -69,6 +87,7 @@ class Server:
         self.device = device
         self.keep_state = keep_state
         self.kc_for = kc_for  # optional callable grid-desc -> k-chunk length (autotuner)
+        self.fill_points = fill_points
         self.stream = torch.cuda.Stream(device=device)
         self.peak_bytes = 0
         self.slices = 0
@@ -105,19 +124,22 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
                 continue
-            key = tuple(c["req"].rid for c in resident)
+            chosen = select_cases(resident, self.fill_points)
+            key = tuple(c["req"].rid for c in chosen)
             if key != batch_key:
                 if batch is not None:
                     batch.close()
-                batch = jz.Batch([c["grid"] for c in resident], stream=self.stream)
+                batch = jz.Batch([c["grid"] for c in chosen], stream=self.stream)
                 batch_key = key
-            n = min(self.slice_steps, min(c["left"] for c in resident))
+            n = min(self.slice_steps, min(c["left"] for c in chosen))
             batch.nsteps(n, self.cfl)
             self.stream.synchronize()
             self.slices += 1
+            advanced = {id(c) for c in chosen}
             still = []
             for c in resident:
-                c["left"] -= n
+                if id(c) in advanced:
+                    c["left"] -= n
                 if c["left"] > 0:
                     still.append(c)
                     continue

@@ -102,3 +102,17 @@ def test_cylinder_blocks_split_in_i_only(L):
         with pytest.raises(jz.JzError) as ei:
             jz.jz_block_bytes(d, o0, o1)
         assert ei.value.code == jz.JZ_EINVAL
+
+
+def test_serving_selection_is_oldest_first_until_filled():
+    from paper_2003_09926_gb300 import serve
+    reqs = [serve.Request(i, W.jet_grid(10 + i, 10, 10), W.jet_flow(), 0, 5, arrival=a)
+            for i, a in enumerate([0.3, 0.1, 0.2, 0.0])]
+    resident = [dict(req=r) for r in reqs]
+    pts = {r.rid: serve.updated_points(r.grid) for r in reqs}
+    assert serve.select_cases(resident, None) == resident
+    one = serve.select_cases(resident, 1)
+    assert [c["req"].rid for c in one] == [3]
+    two = serve.select_cases(resident, pts[3] + 1)
+    assert [c["req"].rid for c in two] == [3, 1]
+    assert [c["req"].rid for c in serve.select_cases(resident, 10**9)] == [3, 1, 2, 0]
