@@ -172,38 +172,6 @@ __global__ void k_fixed_dt(Scalars* sc, double dt) {
   sc->step += 1;
 }
 
-// Combine the per-thread diagnostics records of a block in a fixed order:
-// within each warp a shuffle tree (lane 0's order), then warp 0 combines the
-// warps' records in a second shuffle tree.  The result is valid in thread 0.
-// Sums for words 0..4 and 10, minima for 5 and 7, maxima for 6, 8 and 9.
-__device__ __forceinline__ void diag_combine_step(double a[DIAG_WORDS], int o) {
-  double b[DIAG_WORDS];
-#pragma unroll
-  for (int c = 0; c < DIAG_WORDS; ++c) b[c] = __shfl_down_sync(0xffffffffu, a[c], o);
-#pragma unroll
-  for (int c = 0; c < 5; ++c) a[c] += b[c];
-  a[5] = fmin(a[5], b[5]);
-  a[6] = fmax(a[6], b[6]);
-  a[7] = fmin(a[7], b[7]);
-  a[8] = fmax(a[8], b[8]);
-  a[9] = fmax(a[9], b[9]);
-  a[10] += b[10];
-}
-
-__device__ __forceinline__ void diag_block_combine(double a[DIAG_WORDS], double (*ws)[DIAG_WORDS]) {
-  constexpr int NW = RED_THREADS / 32;
-  for (int o = 16; o > 0; o >>= 1) diag_combine_step(a, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int c = 0; c < DIAG_WORDS; ++c) ws[w][c] = a[c];
-  __syncthreads();
-  if (w == 0) {
-    const double ident[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
-    for (int c = 0; c < DIAG_WORDS; ++c) a[c] = lane < NW ? ws[lane][c] : ident[c];
-    for (int o = NW / 2; o > 0; o >>= 1) diag_combine_step(a, o);
-  }
-}
-
 // Diagnostics partial per thread / block:
 //   [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min, [8] p max,
 //   [9] max of the squared Mach number, [10] non-finite count.
@@ -255,13 +223,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
   }
   double acc[DIAG_WORDS] = {sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value(), sum[4].value(),
                             (double)rmin, (double)rmax, (double)pmin, (double)pmax, (double)m2max, nonfinite};
-  __shared__ double ws[RED_THREADS / 32][DIAG_WORDS];
-  diag_block_combine(acc, ws);
+  __shared__ double sh[DIAG_WORDS][RED_THREADS];
+  for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) {
+      int o = threadIdx.x + half;
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
+      sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
+      sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
+      sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
+      sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
+      sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
+      sh[10][threadIdx.x] += sh[10][o];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0)
-    for (int c = 0; c < DIAG_WORDS; ++c) partial[(long long)blockIdx.x * DIAG_WORDS + c] = acc[c];
+    for (int c = 0; c < DIAG_WORDS; ++c) partial[(long long)blockIdx.x * DIAG_WORDS + c] = sh[c][0];
   if (last_block(&sc->dcount)) {
     // thread t combines block records t, t + 256, ... in order, then the same
-    // fixed combination as above: a fixed summation order whichever block is last
+    // fixed tree as above: a fixed summation order whichever block is last
     const volatile double* P = partial;
     double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
@@ -274,11 +256,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
       r[9] = fmax(r[9], x[9]);
       r[10] += x[10];
     }
-    __syncthreads();  // ws is reused
-    diag_block_combine(r, ws);
+    __syncthreads();
+    for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = r[c];
+    __syncthreads();
+    for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
+      if ((int)threadIdx.x < half) {
+        int o = threadIdx.x + half;
+        for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
+        sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
+        sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
+        sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
+        sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
+        sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
+        sh[10][threadIdx.x] += sh[10][o];
+      }
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
-      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = r[c];
-      sc->diag[9] = sqrt(r[9]);  // maximum Mach number
+      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
+      sc->diag[9] = sqrt(sh[9][0]);  // maximum Mach number
       sc->dcount = 0;
     }
   }
