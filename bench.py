@@ -264,15 +264,15 @@ def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
 def bench_batched(jz, torch, W, local: int, steps: int, steps64: int, cfl: float = 0.5):
     """64 uneven jet grids (32^3 .. 160x128x128), FP32, one persistent launch
     per stage for all grids (graph-replayed), against plain FP64 one grid at a
-    time.  The k-chunk length is chosen by the autotuner."""
+    time.  The tile shape and k-chunk length are chosen by the autotuner."""
     from paper_2003_09926_gb300 import autotune
     cfg = W.config3()
     cases = [(c["grid"], c["flow"]) for c in cfg["cases"]]
-    kc = autotune.tune_batch(cases, cfl=cfl, device=local)
+    choice = autotune.tune_batch(cases, cfl=cfl, device=local)
     stream = torch.cuda.Stream(device=local)
     grids = [jz.Grid(c["grid"], stream=stream, device=local).init(c["flow"], c["seed"]) for c in cfg["cases"]]
     for g in grids:
-        autotune.apply_kc(g, kc)
+        autotune.apply(g, choice)
     pts = sum(interior_points(c["grid"]) for c in cfg["cases"])
     b = jz.Batch(grids, stream=stream)
     b.nsteps(3, cfl)  # warm-up and graph capture
@@ -308,7 +308,8 @@ def bench_batched(jz, torch, W, local: int, steps: int, steps64: int, cfl: float
     v64 = pts * 5 * steps64 / (ms64 / 1e3) / 1e6
     return {"workload": "c3: 64 jet grids 32^3..160x128x128 (seed 3), M~U[1.2,2], Re~U[5e5,2e6]",
             "points_updated": pts, "fp32_batched": {"value": v32, "unit": UNIT, "steps": steps, "ms": ms,
-                                                    "kernel_launches": launches, "kc": kc,
+                                                    "kernel_launches": launches, "kc": choice["kc"],
+                                                    "tile": list(choice["shape"]) if choice["shape"] else None,
                                                     "launches_per_step": launches / steps},
             "fp64_one_grid_at_a_time": {"value": v64, "unit": UNIT, "steps": steps64, "ms": ms64},
             "speedup": v32 / v64}

@@ -328,6 +328,16 @@ int jz_set_tiling(jz_grid* g, int kc);
  * for other variants.  A batch uses its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
+/* Tile shape (ti x tj nodes in i and j) of the FP32 vector-record stage
+ * kernel of this grid: 32 x 16 (default), 16 x 32 or 16 x 16, each a build of
+ * the same kernel (one CTA per SM; 16 x 32 wastes less of a tile on grids
+ * narrow in i, 16 x 16 on small grids).  The per-node arithmetic does not
+ * depend on the shape: results are bitwise the same.  Resets the k-chunk
+ * length to its default for the shape.  A batch needs one shape for all its
+ * grids.  JZ_EINVAL for another shape or for a grid that does not run the
+ * vector-record kernel (JZ_P32 with variant 2). */
+int jz_set_tile_shape(jz_grid* g, int ti, int tj);
+
 /* --- diagnostics without device allocation --------------------------------
  * The paper has no counterpart to this entry point: it serves callers that
  * may only use device arrays they were handed -- a plug-in called by a host

@@ -17,7 +17,12 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_stage_v.cu", "jz_static.cu", "jz_peak.cu", "jz_stats.cu"]
+# (source, object, extra defines): the FP32 vector-record stage kernel is
+# built once per tile shape the autotuner may choose
+SOURCES = [(s, s.replace(".cu", ".o"), []) for s in
+           ("jz_api.cu", "jz_grid.cu", "jz_reduce.cu", "jz_stage.cu", "jz_static.cu", "jz_peak.cu", "jz_stats.cu")]
+SOURCES += [("jz_stage_v.cu", f"jz_stage_v_{ti}x{tj}.o", [f"-DVR_TI={ti}", f"-DVR_TJ={tj}"])
+            for ti, tj in ((32, 16), (16, 32), (16, 16))]
 
 
 def nvcc() -> str:
@@ -36,15 +41,16 @@ def _deps_newer(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, verbose: bool) -> str:
+def _compile(entry, verbose: bool) -> str:
+    src, objname, defines = entry
     path = os.path.join(CSRC, src)
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    obj = os.path.join(BUILD, objname)
     if not _deps_newer(obj, path):
         return obj
     # host code: no fused multiply-add contraction (results that the host
     # forms, such as the statistics' rms, then round as plainly written)
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-           "-c", path, "-o", obj + ".tmp"]
+           *defines, "-c", path, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -268,8 +268,7 @@ int check_dt(double cfl, double dt_fixed) {
 }
 
 // planes per CTA chunk: minimise (waves of resident CTAs) x (planes + prologue)
-int default_kc(const Layout& L, int prec) {
-  StageTiling t = stage_tiling(prec);
+int default_kc(const Layout& L, StageTiling t, int prec) {
   long long tiles = (long long)((L.hi[0] + t.ti) / t.ti) * ((L.hi[1] + t.tj) / t.tj);
   int nz = L.hi[2] - L.lo[2] + 1;
   long long slots = 152LL * stage_ctas_per_sm(prec);
@@ -299,10 +298,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 4-D map over a field array [fields][k][j][i-row of pitch]: box = one plane of
 // (ti+4) x (tj+4) nodes (tile plus two-node halo) x all fields.  Coordinates
 // outside the array read as zero.
-int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int fields, int prec, int halo_rows = 2) {
+int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int fields, StageTiling t,
+                   int halo_rows = 2) {
   auto enc = tensor_map_encoder();
   if (!enc) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-  StageTiling t = stage_tiling(prec);
   const size_t es = fp64 ? 8 : 4;
   cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.n[1] + 2 * NG), (cuuint64_t)(L.n[2] + 2 * NG),
                         (cuuint64_t)fields};
@@ -314,6 +313,25 @@ int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int f
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return JZ_OK;
+}
+
+// TMA maps of the states and metrics for the tile of the kernel the grid runs
+int build_maps(GridDev& d) {
+  const StageTiling t = grid_tiling(d);
+  const bool st64 = d.prec == JZ_P64, mt64 = d.prec == JZ_P64 || d.prec == JZ_P32_M64;
+  int rc;
+  if ((rc = make_plane_map(&d.tmQ[0], d.Q0, st64, d.L, 5, t)) || (rc = make_plane_map(&d.tmQ[1], d.QA, st64, d.L, 5, t)) ||
+      (rc = make_plane_map(&d.tmQ[2], d.QB, st64, d.L, 5, t)) || (rc = make_plane_map(&d.tmM, d.M, mt64, d.L, 10, t)) ||
+      (rc = make_plane_map(&d.tmMv, d.M, mt64, d.L, 10, t, 1)) ||
+      (rc = make_plane_map(&d.tmQ0u, d.Q0, st64, d.L, 5, t, 0)))
+    return rc;
+  return JZ_OK;
+}
+
+void drop_graph(jz_grid* g) {
+  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+  if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
+  g->graph_cfl = g->graph_dt = -1.0;
 }
 
 }  // namespace
@@ -404,8 +422,10 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
   d.partial = (double*)(g->base + cv.off_partial);
   d.inflow = (double*)(g->base + cv.off_inflow);
   d.axis = (double*)(g->base + cv.off_axis);
-  d.kc = default_kc(cv.L, d.prec);
   d.variant = d.prec == JZ_P32 ? 2 : 0;  // P32: the vector-record kernel (fastest measured)
+  d.vti = 32;
+  d.vtj = 16;
+  d.kc = default_kc(cv.L, grid_tiling(d), d.prec);
   const int gn[3] = {desc->ni, desc->nj, desc->nk};
   for (int a = 0; a < 3; ++a) {
     d.goff[a] = g->o0[a];
@@ -447,13 +467,7 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
       tp.m[3 * a + e] = 1 + (int)(splitmix64(desc->map_seed ^ (2 * c)) % 3ULL);
       tp.th[3 * a + e] = 2.0 * 3.14159265358979323846 * unit53(splitmix64(desc->map_seed ^ (2 * c + 1)));
     }
-  const bool st64 = d.prec == JZ_P64, mt64 = d.prec == JZ_P64 || d.prec == JZ_P32_M64;
-  if ((rc = make_plane_map(&d.tmQ[0], d.Q0, st64, cv.L, 5, d.prec)) ||
-      (rc = make_plane_map(&d.tmQ[1], d.QA, st64, cv.L, 5, d.prec)) ||
-      (rc = make_plane_map(&d.tmQ[2], d.QB, st64, cv.L, 5, d.prec)) ||
-      (rc = make_plane_map(&d.tmM, d.M, mt64, cv.L, 10, d.prec)) ||
-      (rc = make_plane_map(&d.tmMv, d.M, mt64, cv.L, 10, d.prec, 1)) ||
-      (rc = make_plane_map(&d.tmQ0u, d.Q0, st64, cv.L, 5, d.prec, 0))) {
+  if ((rc = build_maps(d))) {
     delete g;
     return rc;
   }
@@ -652,7 +666,7 @@ int jz_profile_end(jz_grid* g) {
 
 int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc) {
   if (int rc = check_grid(g, false)) return rc;
-  StageTiling t = stage_tiling(g->dev.prec);
+  StageTiling t = grid_tiling(g->dev);
   if (ti) *ti = t.ti;
   if (tj) *tj = t.tj;
   if (kc) *kc = g->dev.kc;
@@ -664,19 +678,28 @@ int jz_set_stage_variant(jz_grid* g, int variant) {
   if (variant != 0 && variant != 2) return fail(JZ_EINVAL, "stage variant must be 0 or 2");
   if (variant != 0 && g->dev.prec != JZ_P32) return fail(JZ_EINVAL, "stage variant 2 is FP32 (JZ_P32) only");
   g->dev.variant = variant;
-  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
-  if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
-  g->graph_cfl = g->graph_dt = -1.0;
-  return JZ_OK;
+  drop_graph(g);
+  return build_maps(g->dev);  // the two kernels may stage different tiles
+}
+
+int jz_set_tile_shape(jz_grid* g, int ti, int tj) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (g->dev.prec != JZ_P32 || g->dev.variant != 2)
+    return fail(JZ_EINVAL, "the tile shape is chosen for the FP32 vector-record kernel only (JZ_P32, variant 2)");
+  if (!((ti == 32 && tj == 16) || (ti == 16 && tj == 32) || (ti == 16 && tj == 16)))
+    return fail(JZ_EINVAL, "tile shape %d x %d is not one of 32 x 16, 16 x 32, 16 x 16", ti, tj);
+  g->dev.vti = ti;
+  g->dev.vtj = tj;
+  g->dev.kc = default_kc(g->dev.L, grid_tiling(g->dev), g->dev.prec);
+  drop_graph(g);
+  return build_maps(g->dev);
 }
 
 int jz_set_tiling(jz_grid* g, int kc) {
   if (int rc = check_grid(g, false)) return rc;
   if (kc < 1) return fail(JZ_EINVAL, "kc must be >= 1");
   g->dev.kc = kc;
-  if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
-  if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
-  g->graph_cfl = g->graph_dt = -1.0;
+  drop_graph(g);
   return JZ_OK;
 }
 
@@ -703,7 +726,12 @@ int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
     if (prec >= 0 && grids[k]->dev.prec != prec) return fail(JZ_EINVAL, "batch grids must share one precision mode");
     prec = grids[k]->dev.prec;
   }
-  StageTiling t = stage_tiling(prec);
+  const StageTiling t = grid_tiling(grids[0]->dev);
+  for (int k = 1; k < n; ++k) {
+    const StageTiling u = grid_tiling(grids[k]->dev);
+    if (grids[k]->dev.variant != grids[0]->dev.variant || u.ti != t.ti || u.tj != t.tj)
+      return fail(JZ_EINVAL, "batch grids must share one stage kernel and tile shape");
+  }
   std::vector<std::pair<long long, int4>> work;
   for (int k = 0; k < n; ++k) {
     const Layout& L = grids[k]->dev.L;
@@ -819,7 +847,7 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
   if (e != cudaSuccess) return fail(JZ_ECUDA, "batched time step launch failed: %s", cudaGetErrorString(e));
   const int src[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
   for (int l = 0; l < 5; ++l) {
-    e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
+    e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, grid_tiling(b->grids[0]->dev), b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
                            (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
     e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], b->cyl, s);

@@ -28,6 +28,7 @@ struct GridDev {
   int kc;              // planes per CTA chunk of the stage kernel
   int goff[3], gn[3];  // global index of local node 0 and global node counts (blocks; else 0 and n)
   int variant;         // stage kernel of P32: 0 scalar records, 2 vector records
+  int vti, vtj;        // tile shape of the vector-record kernel (32 x 16, 16 x 32 or 16 x 16)
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
   CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)
@@ -97,14 +98,19 @@ cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, 
 // jz_stage.cu
 struct StageTiling { int ti, tj; };
 StageTiling stage_tiling(int prec);
+// the tile of the kernel a grid runs: its chosen shape for the FP32
+// vector-record kernel, else the fixed tile of its precision mode
+inline StageTiling grid_tiling(const GridDev& g) {
+  return (g.prec == JZ_P32 && g.variant == 2) ? StageTiling{g.vti, g.vtj} : stage_tiling(g.prec);
+}
 int stage_ctas_per_sm(int prec);
 // qsel / qout select the input state Q^(l-1) and the output Q^(l): 0 = Q0, 1 = QA, 2 = QB
 cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s);
 // batched stage: a device table of per-grid stage contexts and work items
 size_t stage_ctx_bytes(int prec);
 void stage_ctx_fill(void* host_dst, const GridDev& g);
-cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int4* items, int nitems,
-                               unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s);
+cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const void* ctx, const int4* items,
+                               int nitems, unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s);
 cudaError_t stage_configure();  // one-time kernel attributes (dynamic shared memory)
 
 }  // namespace jz

@@ -641,7 +641,9 @@ cudaError_t stage_configure() {
   if ((e = configure_one<float, double, TIM, TJM>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32>()) != cudaSuccess) return e;
   if ((e = configure_one<float, float, TI32, TJ32, true>()) != cudaSuccess) return e;
-  if ((e = stage_v_configure()) != cudaSuccess) return e;
+  if ((e = stage_v_configure_32x16()) != cudaSuccess) return e;
+  if ((e = stage_v_configure_16x32()) != cudaSuccess) return e;
+  if ((e = stage_v_configure_16x16()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -654,7 +656,10 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
       if (g.variant == 2) {
         StageCtx<float, float> X;
         fill_ctx(X, g);
-        return launch_stage_v(X, StageSel{kRkAlpha[stage], qsel, qout}, s);
+        const StageSel st{kRkAlpha[stage], qsel, qout};
+        if (g.vti == 16 && g.vtj == 32) return launch_stage_v_16x32(X, st, s);
+        if (g.vti == 16 && g.vtj == 16) return launch_stage_v_16x16(X, st, s);
+        return launch_stage_v_32x16(X, st, s);
       }
       return launch_one<float, float, TI32, TJ32>(g, stage, qsel, qout, s);
   }
@@ -676,10 +681,14 @@ void stage_ctx_fill(void* dst, const GridDev& g) {
   }
 }
 
-cudaError_t launch_stage_batch(int prec, int variant, const void* ctx, const int4* items, int nitems,
-                               unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
-  if (prec == JZ_P32 && variant == 2)
-    return launch_stage_v_batch(ctx, items, nitems, queue, StageSel{kRkAlpha[stage], qsel, qout}, s);
+cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const void* ctx, const int4* items,
+                               int nitems, unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
+  if (prec == JZ_P32 && variant == 2) {
+    const StageSel st{kRkAlpha[stage], qsel, qout};
+    if (tile.ti == 16 && tile.tj == 32) return launch_stage_v_batch_16x32(ctx, items, nitems, queue, st, s);
+    if (tile.ti == 16 && tile.tj == 16) return launch_stage_v_batch_16x16(ctx, items, nitems, queue, st, s);
+    return launch_stage_v_batch_32x16(ctx, items, nitems, queue, st, s);
+  }
   switch (prec) {
     case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
     case JZ_P32_M64: return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, s);

@@ -220,9 +220,14 @@ constexpr double kRkAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0}
 
 }  // namespace stg
 
-// FP32 kernel with vector node records (jz_stage_v.cu)
-cudaError_t stage_v_configure();
-cudaError_t launch_stage_v(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s);
-cudaError_t launch_stage_v_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
-                                 const stg::StageSel& st, cudaStream_t s);
+// FP32 kernel with vector node records (jz_stage_v.cu, one build per tile shape)
+#define JZ_STAGE_V_DECL(S)                                                                                    \
+  cudaError_t stage_v_configure_##S();                                                                        \
+  cudaError_t launch_stage_v_##S(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s); \
+  cudaError_t launch_stage_v_batch_##S(const void* ctx, const int4* items, int nitems, unsigned int* queue,      \
+                                       const stg::StageSel& st, cudaStream_t s);
+JZ_STAGE_V_DECL(32x16)
+JZ_STAGE_V_DECL(16x32)
+JZ_STAGE_V_DECL(16x16)
+#undef JZ_STAGE_V_DECL
 }  // namespace jz

@@ -12,8 +12,10 @@
 // inviscid minus viscous flux: the paper's central difference plus
 // dissipation, telescoping exactly.
 //
-// Organisation (one CTA per SM, 2.5-D streaming over a 32 x 16 (i, j) tile
-// and a chunk of k-planes):
+// Organisation (one CTA per SM, 2.5-D streaming over a TI x TJ (i, j) tile
+// and a chunk of k-planes; the file is compiled once per tile shape the
+// autotuner chooses from: 32 x 16, 16 x 32 and 16 x 16, VR_TI / VR_TJ, and
+// its entry points carry the shape in their names):
 //  - TMA stages the conserved variables of one plane (tile plus a two-node
 //    halo) into a planar buffer, and the metric fields of one plane (tile
 //    plus a one-node halo) into a second buffer; waits are bounded;
@@ -34,6 +36,14 @@
 
 #include "jz_stage_common.cuh"
 
+#ifndef VR_TI
+#define VR_TI 32
+#define VR_TJ 16
+#endif
+#define VR_CAT3(a, b, c) a##_##b##x##c
+#define VR_CAT(a, b, c) VR_CAT3(a, b, c)
+#define VR_FN(name) VR_CAT(name, VR_TI, VR_TJ)
+
 namespace jz {
 
 using namespace stg;
@@ -41,10 +51,11 @@ using namespace stg;
 namespace {
 
 namespace vr {
-constexpr int TI = 32, TJ = 16;
-constexpr int NTILE = TI * TJ;                  // 512 tile nodes
+constexpr int TI = VR_TI, TJ = VR_TJ;
+constexpr int NTILE = TI * TJ;                  // tile nodes
 constexpr int NJH = 2 * TI, NIH = 2 * TJ;       // j-halo (rows -1, TJ) and i-halo (columns -1, TI) nodes
-constexpr int NT = NTILE + NJH + NIH;           // 608 threads
+constexpr int NT = NTILE + NJH + NIH;           // threads (608 for 32 x 16 and 16 x 32)
+static_assert(NT % 32 == 0, "whole warps");
 constexpr int NCH = 3 * (NJH + NIH);            // plane elements converted by the halo threads
 constexpr int RW = TI + 4, RH = TJ + 4, PL = RW * RH;  // staged plane: tile + two-node halo (36 x 20)
 constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 36 columns
@@ -637,13 +648,13 @@ __global__ void __launch_bounds__(vr::NT, 1)
 
 }  // namespace
 
-cudaError_t stage_v_configure() {
+cudaError_t VR_FN(stage_v_configure)() {
   cudaError_t e = cudaFuncSetAttribute(k_stage_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_stage_v_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
 }
 
-cudaError_t launch_stage_v(const StageCtx<float, float>& X, const StageSel& st, cudaStream_t s) {
+cudaError_t VR_FN(launch_stage_v)(const StageCtx<float, float>& X, const StageSel& st, cudaStream_t s) {
   const Layout& L = X.L;
   const int nz = L.hi[2] - L.lo[2] + 1;
   dim3 grid((L.hi[0] + vr::TI) / vr::TI, (L.hi[1] + vr::TJ) / vr::TJ, (nz + X.kc - 1) / X.kc);
@@ -652,8 +663,8 @@ cudaError_t launch_stage_v(const StageCtx<float, float>& X, const StageSel& st, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage_v_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue,
-                                 const StageSel& st, cudaStream_t s) {
+cudaError_t VR_FN(launch_stage_v_batch)(const void* ctx, const int4* items, int nitems, unsigned int* queue,
+                                        const StageSel& st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const int ctas = nitems < 152 ? nitems : 152;

@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
             "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "jz_set_tiling": ([G, C.c_int], C.c_int),
             "jz_set_stage_variant": ([G, C.c_int], C.c_int),
+            "jz_set_tile_shape": ([G, C.c_int, C.c_int], C.c_int),
             "jz_fma_peak": ([C.c_int, C.POINTER(C.c_double), VP], C.c_int),
         }
         sig["jz_state_diagnostics_static"] = ([C.c_longlong, C.c_int, VP, VP, C.c_double, VP, VP], C.c_int)
@@ -250,6 +251,10 @@ def jz_set_tiling(h, kc: int) -> None:
 
 def jz_set_stage_variant(h, variant: int) -> None:
     _check(lib().jz_set_stage_variant(h, variant))
+
+
+def jz_set_tile_shape(h, ti: int, tj: int) -> None:
+    _check(lib().jz_set_tile_shape(h, ti, tj))
 
 
 def jz_fma_peak(fp64: bool, stream: int = 0) -> float:

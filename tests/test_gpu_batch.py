@@ -56,3 +56,31 @@ def test_batch_rejects_mixed_precision(jz):
     with pytest.raises(jz.JzError) as ei:
         jz.Batch([a, c], stream=s)
     assert ei.value.code == jz.JZ_EINVAL
+
+
+def test_autotuner_chooses_shape_and_chunk(jz):
+    """The batch autotuner returns one of the built tile shapes and a chunk
+    length; applied to the grids, the batched result is bitwise the default
+    one (the choice changes the schedule, never the arithmetic)."""
+    import torch
+    from paper_2003_09926_gb300 import autotune
+    cases = [(W.jet_grid(34, 18, 16, precision=W.P32), W.jet_flow()),
+             (W.jet_grid(66, 40, 24, precision=W.P32), W.jet_flow(mach=1.6))]
+    choice = autotune.tune_batch(cases)
+    assert choice["shape"] in autotune.SHAPES and choice["kc"] is not None and choice["ms"] > 0
+    stream = torch.cuda.Stream()
+    outs = []
+    for tuned in (False, True):
+        grids = [jz.Grid(d, stream=stream).init(f, 3) for d, f in cases]
+        if tuned:
+            for g in grids:
+                autotune.apply(g, choice)
+        b = jz.Batch(grids, stream=stream)
+        b.nsteps(3, cfl=0.5)
+        stream.synchronize()
+        outs.append([g.download() for g in grids])
+        b.close()
+    for a, c in zip(*outs):
+        np.testing.assert_array_equal(a, c)
+    one = autotune.tune_grid(cases[0][0], cases[0][1])
+    assert one["shape"] in autotune.SHAPES

@@ -324,3 +324,51 @@ def test_fp32_kernel_variants_match_scalar(jz, variant, shape, amp, kc):
     with pytest.raises(jz.JzError):
         g64 = jz.Grid(dict(grid, precision=W.P64)).init(W.jet_flow(), 4)
         jz.jz_set_stage_variant(g64.h, variant)
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (16, 16)])
+def test_tile_shapes_are_bitwise_equal(jz, shape):
+    """The vector-record kernel built for another (i, j) tile evaluates the
+    same per-node arithmetic: the state after 5 steps is bitwise that of the
+    default 32 x 16 tile, on a ragged mapped jet (and with k-chunks of 1 and
+    7 planes)."""
+    grid = W.jet_grid(45, 37, 29, map_amp=0.04, map_seed=3, precision=W.P32)
+    ref = jz.Grid(grid).init(W.jet_flow(re=2e4), 2)
+    ref.nsteps(5, cfl=0.5)
+    want = ref.download()
+    for kc in (None, 1, 7):
+        g = jz.Grid(grid).init(W.jet_flow(re=2e4), 2)
+        jz.jz_set_tile_shape(g.h, *shape)
+        ti, tj, _ = jz.jz_get_tiling(g.h)
+        assert (ti, tj) == shape
+        if kc is not None:
+            jz.jz_set_tiling(g.h, kc)
+        g.nsteps(5, cfl=0.5)
+        np.testing.assert_array_equal(g.download(), want)
+    with pytest.raises(jz.JzError):
+        jz.jz_set_tile_shape(g.h, 64, 8)
+    g64 = jz.Grid(dict(grid, precision=W.P64)).init(W.jet_flow(), 2)
+    with pytest.raises(jz.JzError):
+        jz.jz_set_tile_shape(g64.h, *shape)
+
+
+def test_batch_with_a_tuned_tile_shape(jz):
+    """A batch whose grids run the 16 x 32 tile equals the grids alone; grids
+    of different shapes do not batch."""
+    import torch
+    stream = torch.cuda.Stream()
+    cases = [(W.jet_grid(34, 40, 20, precision=W.P32), 1), (W.jet_grid(50, 33, 17, precision=W.P32), 2)]
+    grids = [jz.Grid(g, stream=stream).init(W.jet_flow(), s) for g, s in cases]
+    for g in grids:
+        jz.jz_set_tile_shape(g.h, 16, 32)
+    b = jz.Batch(grids, stream=stream)
+    b.nsteps(4, cfl=0.5)
+    stream.synchronize()
+    for (d, s), g in zip(cases, grids):
+        alone = jz.Grid(d).init(W.jet_flow(), s)
+        alone.nsteps(4, cfl=0.5)
+        np.testing.assert_array_equal(g.download(), alone.download())
+    b.close()
+    jz.jz_set_tile_shape(grids[1].h, 32, 16)
+    with pytest.raises(jz.JzError):
+        jz.Batch(grids, stream=stream)
