@@ -313,8 +313,9 @@ int jz_fma_peak(int fp64, double* tflops, void* stream);
 
 /* Tile shape of the fused stage kernel for this grid (for tuning and for
  * the batched tile table): ti x tj nodes per CTA, kc planes per CTA chunk.
- * jz_set_tiling may change kc (planes per chunk, >= 1); the tile shape is
- * fixed per precision mode. */
+ * jz_set_tiling may change kc (planes per chunk, >= 1); the (i, j) shape is
+ * fixed per precision mode except for the FP32 vector-record kernel, whose
+ * shape jz_set_tile_shape selects. */
 int jz_get_tiling(jz_grid* g, int* ti, int* tj, int* kc);
 int jz_set_tiling(jz_grid* g, int kc);
 
