@@ -355,20 +355,22 @@ def bench_billion(jz, torch, W, local: int, steps: int, cfl: float = 0.5):
     return out
 
 
-def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6):
-    """Continuous batching on a bounded serving trace: log-uniform 1e5..2e6
-    points per case, 50..500 steps, Poisson arrivals at 70% of the measured
-    batched capacity, 150 GB HBM budget, 10-step slices; against the same
-    trace one case at a time (FP32 unbatched, and FP64 on its first cases)."""
+def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6,
+                  pts_hi: float = 2e6):
+    """Continuous batching on a bounded serving trace: log-uniform 1e5..pts_hi
+    points per case (2e6 by default; the full 2e7 range with --serving-full),
+    50..500 steps, Poisson arrivals at 70% of the measured batched capacity,
+    150 GB HBM budget, 10-step slices; against the same trace one case at a
+    time (FP32 unbatched, and FP64 on its first cases)."""
     from paper_2003_09926_gb300 import serve
-    cfg = W.config4(nreq=nreq, pts_hi=2e6)
+    cfg = W.config4(nreq=nreq, pts_hi=pts_hi)
     work = np.mean([interior_points(r["grid"]) * 5 * r["steps"] for r in cfg["requests"]])
     rate = 0.7 * capacity * 1e6 / work
     trace = serve.poisson_trace(cfg, rate)
     fill = 4 * 10**6
     srv = serve.Server(150 * 10**9, slice_steps=10, device=local, fill_points=fill)
     res = srv.run(trace)
-    out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..2e6 points, 50..500 steps, seed 4",
+    out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..{pts_hi:.0e} points, 50..500 steps, seed 4",
            "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10,
            "fp32_continuous_batching": dict(serve.summarize(res), fill_points=fill,
                                             policy="oldest cases first until they hold fill_points points"),
@@ -426,6 +428,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-cylinder", action="store_true", help="skip the cylindrical-grid measurement")
     ap.add_argument("--no-billion", action="store_true", help="skip the 1e9-point measurement")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serve the full 1e5..2e7-point trace (about a minute) instead of the bounded one")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -571,7 +575,8 @@ def main(argv=None):
         line["batched"] = bench_batched(jz, torch, W, local, steps=max(10, args.steps // 5), steps64=2)
     if not args.no_serving:
         cap = line["batched"]["fp32_batched"]["value"] if "batched" in line else results[head]["value"]
-        line["serving"] = bench_serving(jz, torch, W, local, cap)
+        line["serving"] = (bench_serving(jz, torch, W, local, cap, pts_hi=2e7, base64_n=2) if args.serving_full
+                           else bench_serving(jz, torch, W, local, cap))
     if not args.no_cylinder:
         line["cylinder"] = bench_cylinder(jz, torch, W, local, steps=max(10, args.steps // 4), steps64=2)
     if not args.no_billion and world == 1:

@@ -97,7 +97,7 @@ class Server:
         results: dict[int, Result] = {}
         resident: list[dict] = []
         used = 0
-        batch, batch_key = None, None
+        batches: dict = {}  # member ids -> Batch (its graph is kept while the members stay)
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
         while pending or resident:
@@ -125,14 +125,14 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
                 continue
             chosen = select_cases(resident, self.fill_points)
-            key = tuple(c["req"].rid for c in chosen)
-            if key != batch_key:
-                if batch is not None:
-                    batch.close()
-                batch = jz.Batch([c["grid"] for c in chosen], stream=self.stream)
-                batch_key = key
             n = min(self.slice_steps, min(c["left"] for c in chosen))
-            batch.nsteps(n, self.cfl)
+            if len(chosen) == 1:  # one case: its own graph-replayed steps
+                chosen[0]["grid"].nsteps(n, cfl=self.cfl)
+            else:
+                key = tuple(c["req"].rid for c in chosen)
+                if key not in batches:
+                    batches[key] = jz.Batch([c["grid"] for c in chosen], stream=self.stream)
+                batches[key].nsteps(n, self.cfl)
             self.stream.synchronize()
             self.slices += 1
             advanced = {id(c) for c in chosen}
@@ -152,12 +152,12 @@ class Server:
                 c["grid"].close()
                 used -= c["bytes"]
             if len(still) != len(resident):
+                live = {c["req"].rid for c in still}
+                for key in [k for k in batches if not set(k) <= live]:
+                    batches.pop(key).close()
                 resident = still
-                if batch is not None:
-                    batch.close()
-                batch, batch_key = None, None
-        if batch is not None:
-            batch.close()
+        for b in batches.values():
+            b.close()
         return [results[k] for k in sorted(results)]
 
 
