@@ -335,6 +335,31 @@ def bench_cylinder(jz, torch, W, local: int, steps: int, steps64: int, cfl: floa
     return out
 
 
+def bench_mesh_table(jz, torch, W, local: int, steps: int = 3, cfl: float = 0.5):
+    """The paper's thirteen scalability meshes (Tab. mesh: 32 x 32 x 361 ..
+    1700 x 1700 x 361, 3.7e5 .. 1.0e9 points) as cylindrical jet grids in
+    FP32 on one GPU: per mesh, graph-replayed steps timed with CUDA events,
+    the throughput and its fraction of the HBM roofline at the algorithmic
+    96 B per point-stage."""
+    peak, peak_kind = measured_hbm_peak()
+    rows = []
+    for ni, nj in W.PAPER_MESHES:
+        grid = W.cyl_grid(ni, nj, 361, precision=W.P32)
+        stream = torch.cuda.Stream(device=local)
+        g = jz.Grid(grid, stream=stream, device=local).init(W.jet_flow(), 1)
+        ms, _ = time_steps(jz, torch, g, steps, cfl, 1)
+        pts = interior_points(grid)
+        v = pts * 5 * steps / (ms / 1e3) / 1e6
+        rows.append({"mesh": [ni, nj, 361], "points": ni * nj * 361, "points_updated": pts, "ms_per_step": ms / steps,
+                     "value": v, "hbm_frac": v * 1e6 * 96.0 / (peak * 1e9) if peak else None,
+                     "finite": g.diagnostics()["nonfinite"] == 0})
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    return {"workload": "paper Tab. mesh 1-13 as cylinders (xi x eta x 361), jet, P32", "unit": UNIT,
+            "steps": steps, "hbm_peak_gbs": peak, "peak_kind": peak_kind, "meshes": rows}
+
+
 def bench_billion(jz, torch, W, local: int, steps: int, cfl: float = 0.5):
     """The paper's largest mesh size (Tab. mesh: about 1e9 points) on one GPU:
     c2, 1024 x 1024 x 960 mapped jet in FP32 (state, fluxes and stored
@@ -428,6 +453,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-cylinder", action="store_true", help="skip the cylindrical-grid measurement")
     ap.add_argument("--no-billion", action="store_true", help="skip the 1e9-point measurement")
+    ap.add_argument("--no-mesh-table", action="store_true",
+                    help="skip the paper's thirteen scalability meshes as cylinders (3.7e5 .. 1e9 points, about 10 s)")
     ap.add_argument("--err-steps", type=int, default=200,
                     help="steps of the FP32-vs-FP64 error runs (the 256x192x192 configuration's 200)")
     ap.add_argument("--serving-full", action="store_true",
@@ -584,6 +611,8 @@ def main(argv=None):
         line["cylinder"] = bench_cylinder(jz, torch, W, local, steps=max(10, args.steps // 4), steps64=2)
     if not args.no_billion and world == 1:
         line["billion"] = bench_billion(jz, torch, W, local, steps=max(3, args.steps // 40))
+    if not args.no_mesh_table and world == 1:
+        line["mesh_table"] = bench_mesh_table(jz, torch, W, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_baseline(cfg)
     if rank == 0:

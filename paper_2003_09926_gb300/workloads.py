@@ -55,6 +55,12 @@ def cyl_grid(ni: int, nj: int, nk: int = 361, length: float = 30.0, radius: floa
                 geom=GEOM_CYLINDER)
 
 
+# the paper's scalability meshes (Tab. mesh): points in xi (axial) and eta
+# (radial), all with 361 azimuthal points
+PAPER_MESHES = [(32, 32), (64, 32), (64, 64), (128, 64), (128, 128), (256, 128), (256, 256), (512, 256),
+                (512, 512), (1024, 512), (1024, 1024), (2048, 1024), (1700, 1700)]
+
+
 def periodic_grid(ni: int, nj: int, nk: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), map_amp: float = 0.0,
                   map_seed: int = 0, precision: int = P64) -> dict:
     return dict(ni=ni, nj=nj, nk=nk, bc=list(ALL_PERIODIC), lo=list(lo), hi=list(hi), cluster_r=0.5,
