@@ -183,3 +183,42 @@ def test_cylinder_jet_runs_and_keeps_its_invariants(orc):
     assert np.abs(I[:, :, 0, 1:-1] - I[:, :1, 0, 1:-1]).max() == 0.0
     d = o.diagnostics(Q)
     assert 0.9 < d["rho_min"] <= d["rho_max"] < 1.1 and d["mach_max"] < 1.6
+
+
+def test_cylinder_residual_converges_at_second_order(orc):
+    """Inviscid, no dissipation: J R at the nodes approximates the divergence
+    of the Euler fluxes of a smooth non-axisymmetric field (a Gaussian jet
+    column with swirl-free radial and azimuthal structure), known in closed
+    form (sympy).  Halving every spacing of the polar grid (axial, radial and
+    azimuthal) cuts the error of the mass and energy components by about 4
+    (observed order 1.79 from 32 to 64 intervals, 1.95 from 64 to 128) on the
+    nodes at least two radial lines from the centreline."""
+    import sympy as sp
+    x, y, z = sp.symbols("x y z")
+    g = 1.4
+    r2 = y * y + z * z
+    rho = 1 + sp.Rational(1, 10) * sp.exp(-r2) * sp.cos(x / 2)
+    u = sp.Rational(3, 10) + sp.Rational(1, 5) * sp.sin(2 * x / 5) * sp.exp(-r2)
+    v = sp.Rational(1, 10) * y * sp.exp(-r2)
+    w = sp.Rational(1, 10) * z * sp.exp(-r2) * sp.cos(x / 3)
+    p = (1 + sp.Rational(1, 20) * sp.exp(-r2) * sp.sin(x / 2)) / g
+    E = p / (g - 1) + rho * (u * u + v * v + w * w) / 2
+    div_mass = sp.diff(rho * u, x) + sp.diff(rho * v, y) + sp.diff(rho * w, z)
+    div_en = sp.diff((E + p) * u, x) + sp.diff((E + p) * v, y) + sp.diff((E + p) * w, z)
+    f = [sp.lambdify((x, y, z), e, "numpy") for e in (rho, u, v, w, p, div_mass, div_en)]
+
+    def errors(n):
+        d = W.cyl_grid(n + 1, n // 2 + 1, 2 * n + 1, length=4.0, radius=2.0, stretch_c=0.0)
+        o = orc.Oracle(d, W.jet_flow(re=0.0, cs=0.0, k2=0.0, k4=0.0))
+        X = o.X
+        one = np.ones_like(X[0])
+        Q = np.ascontiguousarray(W.primitive_to_conserved(*[fi(X[0], X[1], X[2]) * one for fi in f[:5]]))
+        o.apply_bc(Q)
+        R, J, Xi = o.inner(o.residual(Q)), o.inner(o.J), o.inner(X)
+        sel = (slice(0, -1), slice(2, -3), slice(3, -3))
+        pts = (Xi[0][sel], Xi[1][sel], Xi[2][sel])
+        return (np.abs(J[sel] * R[0][sel] - f[5](*pts)).max(), np.abs(J[sel] * R[4][sel] - f[6](*pts)).max())
+
+    e1, e2 = errors(32), errors(64)
+    for a, b in zip(e1, e2):
+        assert np.log2(a / b) >= 1.7, (a, b)
