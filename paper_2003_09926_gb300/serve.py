@@ -55,9 +55,14 @@ class Result:
 
 
 def updated_points(grid: dict) -> int:
+    """Nodes the Runge-Kutta stages update (a cylinder's last azimuthal plane
+    repeats its first)."""
     n = 1
     for a, key in enumerate(("ni", "nj", "nk")):
-        n *= grid[key] if grid["bc"][2 * a] == W.BC_PERIODIC else grid[key] - 2
+        if grid["bc"][2 * a] == W.BC_PERIODIC:
+            n *= grid[key] - 1 if (a == 2 and grid.get("geom", W.GEOM_BOX) == W.GEOM_CYLINDER) else grid[key]
+        else:
+            n *= grid[key] - 2
     return n
 
 
