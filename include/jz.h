@@ -267,11 +267,14 @@ int jz_blocks_create(jz_grid* const* blocks, int n, void* dev_buf, size_t bytes,
  * jz_stats_radial: the i-plane whose axial coordinate (at the node nearest the
  *   axis) is nearest x; its nodes binned by r = sqrt(y^2 + z^2) into nbins
  *   equal bins of [0, r_max): per bin the mean of <U>, the mean of u_rms and
- *   the node count (empty bins 0).
- * jz_stats_core_length: <U> on the axis (the mean over the node lines nearest
- *   y = z = 0: the middle line of an odd node count, both middle lines of an
- *   even one) and the axial distance from the inlet to its first drop below
- *   frac * u_jet, interpolated linearly (the last node's x if it never drops).
+ *   the node count (empty bins 0; a cylinder's last azimuthal plane, a copy
+ *   of the first, is not counted).
+ * jz_stats_core_length: <U> on the axis (on a box the mean over the node
+ *   lines nearest y = z = 0: the middle line of an odd node count, both
+ *   middle lines of an even one; on a cylinder the mean over the centreline's
+ *   P distinct azimuths) and the axial distance from the inlet to its first
+ *   drop below frac * u_jet, interpolated linearly (the last node's x if it
+ *   never drops).
  * The read functions synchronise the grid's stream; JZ_EINVAL without samples
  * or for bad arguments.
  * jz_set_clock sets the grid's simulated time and step count (restarting from

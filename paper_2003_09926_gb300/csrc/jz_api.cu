@@ -1110,6 +1110,8 @@ int jz_stats_radial(jz_stats* s, double x, int nbins, double r_max, double* mean
   for (int i = 1; i < n0; ++i)
     if (std::fabs(xs[i] - x) < std::fabs(xs[ip] - x)) ip = i;
   const size_t m = (size_t)n1 * n2;
+  // a cylinder's last azimuthal plane repeats its first: not binned twice
+  const size_t mb = s->g->dev.L.cyl ? (size_t)n1 * (size_t)s->g->dev.L.pn[2] : m;
   std::vector<double> yz(2 * m), su(m), su2(m);
   JZ_CUDA(launch_stats_plane_yz(s->g->dev, ip, s->scr, st));
   JZ_CUDA(cudaMemcpyAsync(yz.data(), s->scr, 16 * m, cudaMemcpyDeviceToHost, st));
@@ -1118,7 +1120,7 @@ int jz_stats_radial(jz_stats* s, double x, int nbins, double r_max, double* mean
   JZ_CUDA(cudaStreamSynchronize(st));
   for (int b = 0; b < nbins; ++b) mean_u[b] = rms_u[b] = count[b] = 0.0;
   const double ns = (double)s->samples;
-  for (size_t t = 0; t < m; ++t) {  // nodes in [k][j] order
+  for (size_t t = 0; t < mb; ++t) {  // nodes in [k][j] order
     const double r = std::sqrt(yz[2 * t] * yz[2 * t] + yz[2 * t + 1] * yz[2 * t + 1]);
     if (!(r < r_max)) continue;
     const int b = std::min(nbins - 1, (int)(r / r_max * nbins));
@@ -1142,22 +1144,30 @@ int jz_stats_core_length(jz_stats* s, double u_jet, double frac, double* length)
   const Layout& L = s->g->dev.L;
   const int n0 = L.n[0], n1 = L.n[1];
   cudaStream_t st = s->g->stream;
-  int cj[2], ck[2], mj, mk;
-  axis_nodes(L.n[1], cj, mj);
-  axis_nodes(L.n[2], ck, mk);
+  // the node lines of the axis: on a box the one, two or four lines nearest
+  // y = z = 0; on a cylinder the centreline j = 0 at its P distinct azimuths
+  std::vector<std::pair<int, int>> lines;
+  if (L.cyl) {
+    for (int k = 0; k < L.pn[2]; ++k) lines.push_back({0, k});
+  } else {
+    int cj[2], ck[2], mj, mk;
+    axis_nodes(L.n[1], cj, mj);
+    axis_nodes(L.n[2], ck, mk);
+    for (int a = 0; a < mj; ++a)
+      for (int b = 0; b < mk; ++b) lines.push_back({cj[a], ck[b]});
+  }
   std::vector<double> xs(n0), axis(n0, 0.0), line(n0);
-  JZ_CUDA(launch_stats_axis_x(s->g->dev, cj[0], ck[0], s->scr, st));
+  JZ_CUDA(launch_stats_axis_x(s->g->dev, lines[0].first, lines[0].second, s->scr, st));
   JZ_CUDA(cudaMemcpyAsync(xs.data(), s->scr, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
   JZ_CUDA(cudaStreamSynchronize(st));
-  // <U> on the axis: the mean over the one, two or four node lines around it
-  for (int a = 0; a < mj; ++a)
-    for (int b = 0; b < mk; ++b) {
-      const size_t off = (size_t)n0 * (cj[a] + (size_t)n1 * ck[b]);
-      JZ_CUDA(cudaMemcpyAsync(line.data(), s->su + off, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
-      JZ_CUDA(cudaStreamSynchronize(st));
-      for (int i = 0; i < n0; ++i) axis[i] += line[i];
-    }
-  const double level = frac * u_jet, ns = (double)s->samples * mj * mk;
+  // <U> on the axis: the mean over those lines
+  for (const auto& jk : lines) {
+    const size_t off = (size_t)n0 * (jk.first + (size_t)n1 * jk.second);
+    JZ_CUDA(cudaMemcpyAsync(line.data(), s->su + off, 8 * (size_t)n0, cudaMemcpyDeviceToHost, st));
+    JZ_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n0; ++i) axis[i] += line[i];
+  }
+  const double level = frac * u_jet, ns = (double)s->samples * (double)lines.size();
   for (int i = 0; i < n0; ++i) axis[i] /= ns;
   // the first crossing below frac * u_jet from the inlet, interpolated linearly
   double len = xs[n0 - 1];

@@ -118,3 +118,34 @@ def test_restart_continues_bitwise(jz, prec, tmp_path):
     assert d["step"] == dwant["step"] == 6 and d["time"] == dwant["time"] and d["dt"] == dwant["dt"]
     a.close()
     b.close()
+
+
+def test_cylinder_statistics(jz):
+    """On the cylinder the axis is the centreline j = 0 (mean over its
+    azimuths) and the radial profile bins each distinct node once: the
+    closed-form core length of a linearly decaying axial velocity, and bin
+    counts equal to the node count of each radius band."""
+    ni, nj, nk = 61, 9, 13
+    grid = W.cyl_grid(ni, nj, nk, length=30.0, radius=8.0, stretch_c=0.0)  # x_i = 0.5 i, r_j = j
+    flow = W.jet_flow()
+    M, gam = flow["mach"], flow["gamma"]
+    g = jz.Grid(grid).init(flow, 0)
+    x = 30.0 * np.arange(ni) / (ni - 1)
+    gx = np.where(x <= 4.0, 1.0, np.maximum(0.5, 1.0 - 0.05 * (x - 4.0)))
+    u = np.broadcast_to(M * gx, (nk, nj, ni))
+    Q = np.empty((5, nk, nj, ni))
+    Q[0] = 1.0
+    Q[1] = u
+    Q[2] = Q[3] = 0.0
+    Q[4] = 1.0 / (gam * (gam - 1.0)) + 0.5 * u * u
+    g.upload(Q)
+    st = jz.Stats(g)
+    st.sample()
+    assert st.core_length(M, 0.95) == pytest.approx(5.0, abs=1e-12)
+    nb, rmax = 5, 3.9  # r_j = j, bins 0.78 wide: j = 0, 1, 2, 3 in bins 0..3 (away from the edges), bin 4 empty
+    pm, pr, pc = st.radial(5.0, nb, rmax)
+    P = nk - 1
+    np.testing.assert_array_equal(pc, [P, P, P, P, 0])
+    np.testing.assert_allclose(pm[:4], 0.95 * M, rtol=1e-12)  # the plane x = 5, where u = 0.95 M
+    st.close()
+    g.close()
