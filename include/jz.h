@@ -207,6 +207,16 @@ int jz_nsteps(jz_grid* g, int n, double cfl, double dt_fixed);
  * node holds a non-finite value. */
 int jz_diagnostics(jz_grid* g, jz_diag* out);
 
+/* The diagnostics of jz_diagnostics, enqueued on the grid's stream with their
+ * copy to *out, without synchronising: *out holds them once the stream has
+ * passed the copy (after a stream synchronisation or an event recorded after
+ * this call).  The copy overlaps later work on the stream only when *out is
+ * page-locked host memory (cudaHostAlloc, or a pinned torch tensor); *out
+ * must stay valid until the copy has run.  Non-finite values are reported in
+ * out->nonfinite only, and a bounded-wait timeout of the stage kernel only
+ * by the next jz_diagnostics.  JZ_EINVAL for a null handle or output. */
+int jz_diagnostics_async(jz_grid* g, jz_diag* out);
+
 /* Copy the state to host memory: n = 5*ni*nj*nk doubles, layout [v][k][j][i]
  * (conserved rho, rho u, rho v, rho w, e), ghosts excluded; FP32 states are
  * widened (JZ_P32_S64: the updated nodes come from the FP64 state, boundary

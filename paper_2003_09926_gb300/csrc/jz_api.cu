@@ -600,6 +600,14 @@ int jz_diagnostics(jz_grid* g, jz_diag* out) {
   return JZ_OK;
 }
 
+int jz_diagnostics_async(jz_grid* g, jz_diag* out) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (!out) return fail(JZ_EINVAL, "null output");
+  JZ_CUDA(launch_diagnostics(g->dev, g->stream));
+  JZ_CUDA(cudaMemcpyAsync(out, &g->dev.sc->out, sizeof(jz_diag), cudaMemcpyDeviceToHost, g->stream));
+  return JZ_OK;
+}
+
 static size_t state_count(const jz_grid* g) {
   const Layout& L = g->dev.L;  // the grid's (a block's) own nodes
   return 5ULL * (size_t)L.n[0] * (size_t)L.n[1] * (size_t)L.n[2];

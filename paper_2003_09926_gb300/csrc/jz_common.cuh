@@ -103,6 +103,7 @@ struct Scalars {
   int err;            // sticky device error flag
   int errinfo[7];     // first failure: barrier, parity, plane, tile x, tile y, chunk, stage input
   double diag[16];    // diagnostics result
+  jz_diag out;        // the same in the public layout (copied out by jz_diagnostics_async)
 };
 
 constexpr int RED_BLOCKS = 1216;  // fixed grid of the reductions (8 x 152 SMs)

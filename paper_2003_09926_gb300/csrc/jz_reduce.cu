@@ -275,6 +275,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
     if (threadIdx.x == 0) {
       for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
       sc->diag[9] = sqrt(sh[9][0]);  // maximum Mach number
+      jz_diag& o = sc->out;
+      o.time = sc->time;
+      o.step = sc->step;
+      o.dt = sc->dt;
+      for (int v = 0; v < 5; ++v) o.sum[v] = sc->diag[v];
+      o.rho_min = sc->diag[5];
+      o.rho_max = sc->diag[6];
+      o.p_min = sc->diag[7];
+      o.p_max = sc->diag[8];
+      o.mach_max = sc->diag[9];
+      o.nonfinite = (int64_t)sc->diag[10];
       sc->dcount = 0;
     }
   }

@@ -68,6 +68,7 @@ def lib() -> C.CDLL:
             "jz_rk_step": ([G, C.c_double, C.c_double], C.c_int),
             "jz_nsteps": ([G, C.c_int, C.c_double, C.c_double], C.c_int),
             "jz_diagnostics": ([G, C.POINTER(Diag)], C.c_int),
+            "jz_diagnostics_async": ([G, VP], C.c_int),
             "jz_state_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_state_upload": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_batch_bytes": ([C.POINTER(G), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
@@ -207,6 +208,26 @@ def jz_diagnostics(h, allow_nonfinite: bool = False) -> dict:
             "nonfinite": d.nonfinite, "status": rc}
 
 
+def diag_dict(d: Diag) -> dict:
+    return {"time": d.time, "step": d.step, "dt": d.dt, "sum": np.array(list(d.sum)), "rho_min": d.rho_min,
+            "rho_max": d.rho_max, "p_min": d.p_min, "p_max": d.p_max, "mach_max": d.mach_max,
+            "nonfinite": d.nonfinite}
+
+
+class PinnedDiag:
+    """A jz_diag record in page-locked host memory (a pinned torch tensor), the
+    target of Grid.diagnostics_async."""
+
+    def __init__(self):
+        torch = _torch()
+        self._buf = torch.zeros(C.sizeof(Diag), dtype=torch.uint8, pin_memory=True)
+        self.ptr = self._buf.data_ptr()
+
+    def read(self) -> dict:
+        """The record as a dict (valid once the stream has passed the copy)."""
+        return diag_dict(Diag.from_address(self.ptr))
+
+
 def jz_state_download(h, out: np.ndarray) -> np.ndarray:
     assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
     _check(lib().jz_state_download(h, out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
@@ -318,6 +339,11 @@ class Grid:
 
     def diagnostics(self, allow_nonfinite: bool = False) -> dict:
         return jz_diagnostics(self.h, allow_nonfinite)
+
+    def diagnostics_async(self, out: "PinnedDiag") -> None:
+        """Enqueue the diagnostics and their copy into out on the grid's
+        stream (no synchronisation; read out after the stream passes it)."""
+        _check(lib().jz_diagnostics_async(self.h, C.c_void_p(out.ptr)))
 
     def download(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:

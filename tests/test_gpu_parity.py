@@ -372,3 +372,20 @@ def test_batch_with_a_tuned_tile_shape(jz):
     jz.jz_set_tile_shape(grids[1].h, 32, 16)
     with pytest.raises(jz.JzError):
         jz.Batch(grids, stream=stream)
+
+
+def test_async_diagnostics_equal_the_synchronous_ones(jz):
+    """jz_diagnostics_async enqueues the same reduction; its record, read after
+    the stream passes the copy, equals jz_diagnostics bitwise."""
+    grid = W.jet_grid(40, 24, 20, map_amp=0.03, map_seed=2, precision=W.P32)
+    g = jz.Grid(grid).init(W.jet_flow(), 5)
+    g.nsteps(3, cfl=0.5)
+    rec = jz.PinnedDiag()
+    g.diagnostics_async(rec)
+    g.stream.synchronize()
+    a = rec.read()
+    b = g.diagnostics()
+    for k in ("time", "step", "dt", "rho_min", "rho_max", "p_min", "p_max", "mach_max", "nonfinite"):
+        assert a[k] == b[k], k
+    np.testing.assert_array_equal(a["sum"], b["sum"])
+    assert a["step"] == 3
