@@ -66,3 +66,11 @@ def test_reference_arm_prints_one_line_on_rank0(capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "Mpt-stage/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_is_silent_on_other_ranks(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.argparse.Namespace(gpus=2, steps=1, warmup=0)
+    assert bench.run_reference(args, 1, 2) == 0
+    assert capsys.readouterr().out.strip() == ""
