@@ -325,6 +325,7 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
         if (idx[d] == ((ff % 2 == 0) ? 0 : L.n[d] - 1)) f = ff;
       }
       face[u] = f;
+      if (f < 0) continue;  // not reached: a node outside the updated box lies on some face
       if (L.bc[f] == BC_INFLOW) {  // x- face only: profile tabulated per (j, k)
         kind[u] = 1;
         inf[u] = mk * L.n[1] + mj;
