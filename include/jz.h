@@ -12,10 +12,14 @@
  *                                               curvilinear coordinates, anisotropic
  *                                               scalar dissipation (Turkel & Vatsa),
  *                                               explicit 5-stage Runge-Kutta
- *   Section 3 (boundary-condition paragraph)    supersonic inflow, Riemann far field
+ *   Section 3 (boundary-condition paragraph)    supersonic inflow, Riemann far field,
+ *                                               the cylindrical domain's centreline
+ *                                               (extrapolation plus azimuthal average)
+ *                                               and superposed azimuthal points
  *   Section 4.2, Fig. jazzy                     per stage: boundary update,
  *                                               inviscid flux, dissipation, viscous flux
  *   Section 4.3                                 two-layer ghost fringe, five-point stencil
+ *   Section 6                                   time statistics of the jet
  *
  * Conventions shared by every entry point:
  *  - Every function returns an int status: JZ_OK (0) or a negative JZ_E* code.
