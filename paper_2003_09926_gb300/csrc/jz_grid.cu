@@ -395,22 +395,66 @@ __global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constan
 // Centreline of a cylindrical grid (the paper's singularity treatment,
 // Section 3 and Section 4.3): for every axial index i and variable v, the
 // mean of Q_v over the P distinct azimuthal nodes of the radial line j = 1,
-// summed in azimuthal order in FP64 (one thread per (i, v): the sequential
-// order the paper keeps for bitwise reproducibility).
-template <typename ST>
-__device__ __forceinline__ void axis_mean(const Layout& L, const ST* __restrict__ Q, double* __restrict__ axis) {
-  const int n = 5 * L.n[0];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int v = t / L.n[0], i = t - v * L.n[0];
-    const ST* q = Q + (long long)v * L.npad + L.at(i, 1, 0);
-    double s = 0.0;
-    for (int k = 0; k < L.pn[2]; ++k) s += (double)q[(long long)k * L.plane];
-    axis[t] = s / L.pn[2];
+// summed in azimuthal order in FP64 -- the sequential order the paper keeps
+// so that a partitioned run reproduces the serial one bit for bit.
+// A block takes 32 consecutive i of one variable (blockIdx.y).  The loads
+// are issued in parallel: the azimuth goes through shared memory in chunks
+// of 24 KB (192 FP32 or 96 FP64 values per i), seven warps loading the next
+// chunk (one coalesced row of 32 i per load) while warp 0 adds the current
+// one, lane = i, value by value in azimuthal order.
+constexpr int AX_WARPS = 8;
+constexpr int AX_BYTES = 24576;  // one chunk buffer; two are used
+
+// rows first + r, r = wr, wr + NW, ... < m, of the 32 i-columns into dst[r]:
+// all loads of a warp issued before the first store
+template <typename ST, int NW, int CH>
+__device__ __forceinline__ void ax_load(ST (*dst)[32], const ST* q, long long plane, int first, int m, int wr,
+                                        bool live, int lane) {
+  constexpr int U = (CH + NW - 1) / NW;
+  ST x[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int r = wr + u * NW;
+    x[u] = (live && r < m) ? q[(long long)(first + r) * plane] : ST(0);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int r = wr + u * NW;
+    if (r < m) dst[r][lane] = x[u];
   }
 }
 
 template <typename ST>
-__global__ void k_axis_mean(const __grid_constant__ Layout L, const ST* __restrict__ Q, double* __restrict__ axis) {
+__device__ __forceinline__ void axis_mean(const Layout& L, const ST* __restrict__ Q, double* __restrict__ axis) {
+  constexpr int CH = AX_BYTES / (32 * (int)sizeof(ST));
+  __shared__ ST buf[2][CH][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int v = blockIdx.y, P = L.pn[2], nch = (P + CH - 1) / CH;
+  for (int bx = blockIdx.x; bx * 32 < L.n[0]; bx += gridDim.x) {  // block-uniform trip count
+    const int i = bx * 32 + lane;
+    const bool live = i < L.n[0];
+    const ST* q = Q + (long long)v * L.npad + L.at(live ? i : 0, 1, 0);
+    ax_load<ST, AX_WARPS, CH>(buf[0], q, L.plane, 0, min(CH, P), w, live, lane);  // chunk 0: every warp
+    __syncthreads();
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) {
+      const int base = c * CH, m = min(CH, P - base);
+      if (w == 0) {
+        const ST* b = &buf[c & 1][0][lane];
+        for (int r = 0; r < m; ++r) s += (double)b[r * 32];
+      } else if (c + 1 < nch) {
+        ax_load<ST, AX_WARPS - 1, CH>(buf[(c + 1) & 1], q, L.plane, base + CH, min(CH, P - base - CH), w - 1, live,
+                                      lane);
+      }
+      __syncthreads();
+    }
+    if (w == 0 && live) axis[v * L.n[0] + i] = s / P;
+  }
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(32 * AX_WARPS) k_axis_mean(const __grid_constant__ Layout L, const ST* __restrict__ Q,
+                                                             double* __restrict__ axis) {
   axis_mean<ST>(L, Q, axis);
 }
 
@@ -432,7 +476,7 @@ __global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
 }
 
 template <typename ST>
-__global__ void k_axis_mean_batch(const BcCtx* __restrict__ ctx, int which) {
+__global__ void __launch_bounds__(32 * AX_WARPS) k_axis_mean_batch(const BcCtx* __restrict__ ctx, int which) {
   const BcCtx& X = ctx[blockIdx.z];
   if (X.L.cyl) axis_mean<ST>(X.L, (const ST*)X.Q[which], X.axis);
 }
@@ -637,11 +681,11 @@ cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
   const Slabs sl = bc_slabs(g.L);
   const dim3 b(slab_blocks(sl), 6);
   if (g.L.cyl) {
-    const int ab = (5 * g.L.n[0] + 127) / 128;
+    const dim3 ab((g.L.n[0] + 31) / 32, 5);
     if (g.prec == JZ_P64)
-      k_axis_mean<double><<<ab, 128, 0, s>>>(g.L, (const double*)Q, g.axis);
+      k_axis_mean<double><<<ab, 32 * AX_WARPS, 0, s>>>(g.L, (const double*)Q, g.axis);
     else
-      k_axis_mean<float><<<ab, 128, 0, s>>>(g.L, (const float*)Q, g.axis);
+      k_axis_mean<float><<<ab, 32 * AX_WARPS, 0, s>>>(g.L, (const float*)Q, g.axis);
     count_launches(1);
   }
   switch (g.prec) {
@@ -680,11 +724,11 @@ cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int wh
   const dim3 b(blocks, 6, n);
   const BcCtx* X = (const BcCtx*)ctx;
   if (cyl) {  // some grid of the batch is cylindrical: centreline means first
-    const dim3 ab(8, 1, n);
+    const dim3 ab(8, 5, n);
     if (prec == JZ_P64)
-      k_axis_mean_batch<double><<<ab, 128, 0, s>>>(X, which);
+      k_axis_mean_batch<double><<<ab, 32 * AX_WARPS, 0, s>>>(X, which);
     else
-      k_axis_mean_batch<float><<<ab, 128, 0, s>>>(X, which);
+      k_axis_mean_batch<float><<<ab, 32 * AX_WARPS, 0, s>>>(X, which);
     count_launches(1);
   }
   switch (prec) {
