@@ -89,7 +89,9 @@ extern "C" {
 
 /* Grid descriptor.  Nodes are numbered 0..n-1 per direction (i fastest);
  * non-periodic directions need n >= 3 and their first and last nodes are
- * boundary nodes set by the boundary conditions.
+ * boundary nodes set by the boundary conditions.  At most 2^24 nodes per
+ * direction, and nj * nk * ceil(ni / 32) below 2^31 (the reductions index
+ * rows of 32 nodes with 32-bit integers).
  *
  * JZ_GEOM_BOX: x is uniform on [lo[0], hi[0]]; y and z (when not periodic
  * and stretch_c > 0) follow a tanh clustering about |y| = cluster_r; every

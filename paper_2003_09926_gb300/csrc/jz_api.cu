@@ -78,6 +78,8 @@ static int validate(const jz_grid_desc* d) {
   }
   for (int f = 1; f < 6; ++f)
     if (d->bc[f] == JZ_BC_INFLOW) return fail(JZ_EINVAL, "the inflow condition is supported on the x- face only");
+  if ((long long)d->nj * d->nk * ((d->ni + 31) / 32) >= (1LL << 31))
+    return fail(JZ_EINVAL, "grid too large: nj * nk * ceil(ni / 32) must stay below 2^31");
   if (d->precision != JZ_P64 && d->precision != JZ_P32_M64 && d->precision != JZ_P32 && d->precision != JZ_P32_S64)
     return fail(JZ_EINVAL, "bad precision mode %d", d->precision);
   if (d->stretch_c != 0.0 && !(d->stretch_w > 0.0)) return fail(JZ_EINVAL, "stretch_w must be > 0");

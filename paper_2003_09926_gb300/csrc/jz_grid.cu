@@ -6,6 +6,7 @@
 // Section 4.2 (Jacobian and metric terms computed once after the mesh is
 // read; boundary update at the start of every Runge-Kutta stage) and
 // Section 4.3 (two-layer ghost fringe).
+#include <climits>
 #include <cmath>
 
 #include "jz_internal.h"
@@ -452,10 +453,97 @@ __device__ __forceinline__ void axis_mean(const Layout& L, const ST* __restrict_
   }
 }
 
+// FP32 state.  Every partial sum of the sequential order is a multiple of
+// 2^e, e the exponent of the unit in the last place of the smallest nonzero
+// value, and at most sum |x| in magnitude; when that bound is below 2^(e+53)
+// no partial sum rounds in FP64, so the sequential result is the exact sum,
+// formed here as an integer sum of x / 2^e in any order (all warps, one pass
+// for the exponent and the bound, one for the sum).  Otherwise, and for
+// non-finite values, warp 0 runs the sequential chain.  On GB300 a warp-wide
+// FP64 add or conversion occupies the FP64 pipe for many cycles, so the
+// chain of P of them took about 30 us per launch on its own.
+__device__ __forceinline__ void axis_mean_f32(const Layout& L, const float* __restrict__ Q, double* __restrict__ axis) {
+  __shared__ int s_emin[AX_WARPS][32];
+  __shared__ float s_abs[AX_WARPS][32];
+  __shared__ long long s_acc[AX_WARPS][32];
+  __shared__ int s_exact[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int v = blockIdx.y, P = L.pn[2];
+  for (int bx = blockIdx.x; bx * 32 < L.n[0]; bx += gridDim.x) {  // block-uniform trip count
+    const int i = bx * 32 + lane;
+    const bool live = i < L.n[0];
+    const float* q = Q + (long long)v * L.npad + L.at(live ? i : 0, 1, 0);
+    int emin = INT_MAX;  // exponent of the smallest unit in the last place (nonzero values)
+    float sabs = 0.f;    // sum of magnitudes; +inf marks a non-finite value
+    if (live) {
+#pragma unroll 12
+      for (int k = w; k < P; k += AX_WARPS) {
+        const unsigned b = __float_as_uint(q[(long long)k * L.plane]);
+        const int E = (int)((b >> 23) & 0xffu);
+        if (E == 255) sabs = INFINITY;
+        if ((b & 0x7fffffffu) != 0u) emin = min(emin, E == 0 ? -149 : E - 150);
+        sabs += __uint_as_float(b & 0x7fffffffu);
+      }
+    }
+    s_emin[w][lane] = emin;
+    s_abs[w][lane] = sabs;
+    __syncthreads();
+    if (w == 0) {
+      int em = INT_MAX;
+      float sa = 0.f;
+      for (int r = 0; r < AX_WARPS; ++r) {
+        em = min(em, s_emin[r][lane]);
+        sa += s_abs[r][lane];
+      }
+      // the FP32 sum of P magnitudes is within a factor 1 + 2 P 2^-24 of the true sum
+      const bool exact = em == INT_MAX ||
+                         (isfinite(sa) && (double)sa * (1.0 + 2.0 * P * 0x1p-24) < ldexp(1.0, em + 53));
+      s_exact[lane] = exact;
+      s_emin[0][lane] = em;
+    }
+    __syncthreads();
+    const int em = s_emin[0][lane];
+    const bool exact = s_exact[lane] != 0;
+    long long acc = 0;
+    if (live && exact && em != INT_MAX) {
+#pragma unroll 12
+      for (int k = w; k < P; k += AX_WARPS) {
+        const unsigned b = __float_as_uint(q[(long long)k * L.plane]);
+        const int E = (int)((b >> 23) & 0xffu);
+        const long long m = (long long)((b & 0x7fffffu) | (E ? 0x800000u : 0u));
+        const long long t = m << ((E == 0 ? -149 : E - 150) - em);  // < 2^53 by the bound
+        acc += (b >> 31) ? -t : t;
+      }
+    }
+    s_acc[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && live) {
+      double s = 0.0;
+      if (exact) {
+        long long t = 0;
+        for (int r = 0; r < AX_WARPS; ++r) t += s_acc[r][lane];
+        s = em == INT_MAX ? 0.0 : ldexp((double)t, em);
+      } else {
+        for (int k = 0; k < P; ++k) s += (double)q[(long long)k * L.plane];
+      }
+      axis[v * L.n[0] + i] = s / P;
+    }
+    __syncthreads();  // the shared arrays are reused by the next 32 columns
+  }
+}
+
+template <typename ST>
+__device__ __forceinline__ void axis_mean_any(const Layout& L, const ST* __restrict__ Q, double* __restrict__ axis) {
+  if constexpr (sizeof(ST) == 4)
+    axis_mean_f32(L, Q, axis);
+  else
+    axis_mean<ST>(L, Q, axis);
+}
+
 template <typename ST>
 __global__ void __launch_bounds__(32 * AX_WARPS) k_axis_mean(const __grid_constant__ Layout L, const ST* __restrict__ Q,
                                                              double* __restrict__ axis) {
-  axis_mean<ST>(L, Q, axis);
+  axis_mean_any<ST>(L, Q, axis);
 }
 
 // batched versions: grid blockIdx.z of the table, state copy `which`
@@ -478,7 +566,7 @@ __global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
 template <typename ST>
 __global__ void __launch_bounds__(32 * AX_WARPS) k_axis_mean_batch(const BcCtx* __restrict__ ctx, int which) {
   const BcCtx& X = ctx[blockIdx.z];
-  if (X.L.cyl) axis_mean<ST>(X.L, (const ST*)X.Q[which], X.axis);
+  if (X.L.cyl) axis_mean_any<ST>(X.L, (const ST*)X.Q[which], X.axis);
 }
 
 // Halo exchange between blocks of one grid (the paper's ghost exchange,

@@ -60,29 +60,49 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
   // the maximum is taken in the arithmetic type: exact, and the same value
   // as a maximum of the widened rates
   ST best_s = ST(0);
-  // warp w of the fixed grid visits rows r = w, w + W, ... (r = j + nj k);
-  // lanes walk i, four nodes per lane at a time with all their loads issued
-  // before any arithmetic (the kernel is bound by memory latency)
+  // the nodes are taken as items of 32 consecutive i (item = ch + nch (j +
+  // nj k), ch the chunk of i); warp w of the fixed grid takes items 4w ..
+  // 4w + 3, then the next four after all warps, one node per lane and item,
+  // with the loads of all four issued before any arithmetic (the kernel is
+  // bound by memory latency; on a narrow grid the four are rows, on a wide
+  // one parts of a row).  The item counter moves as (ch, j, k) with carries:
+  // no division inside the loop.
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
+  const int nch = (L.n[0] + 31) >> 5;
+  const long long items = (long long)L.n[1] * L.n[2] * nch;  // < 2^31, checked when the grid is created
   const int W = (gridDim.x * blockDim.x) >> 5;
-  const int rows = L.n[1] * L.n[2];
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += W) {
-    const long long row = L.at(0, r % L.n[1], r / L.n[1]);
-    for (int ib = 0; ib < L.n[0]; ib += 32 * U) {
-      ST q[U][5], m[U][10];
+  const int first = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * U;
+  const int stride = W * U;
+  int ch = first % nch, j = (first / nch) % L.n[1], k = first / nch / L.n[1];
+  const int dch = stride % nch, dj = (stride / nch) % L.n[1], dk = stride / nch / L.n[1];
+  for (long long it0 = first; it0 < items; it0 += stride) {
+    ST q[U][5], m[U][10];
+    bool live[U];
+    int cu = ch, ju = j, ku = k;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = ib + lane + 32 * u;
-        const long long n = row + (i < L.n[0] ? i : 0);
+    for (int u = 0; u < U; ++u) {
+      const int i = cu * 32 + lane;
+      live[u] = it0 + u < items && i < L.n[0];
+      const long long n = live[u] ? L.at(i, ju, ku) : L.at(0, 0, 0);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) q[u][v] = Q[v * L.npad + n];
+      for (int v = 0; v < 5; ++v) q[u][v] = Q[v * L.npad + n];
 #pragma unroll
-        for (int f = 0; f < 10; ++f) m[u][f] = (ST)M[f * L.npad + n];
+      for (int f = 0; f < 10; ++f) m[u][f] = (ST)M[f * L.npad + n];
+      if (++cu == nch) {
+        cu = 0;
+        if (++ju == L.n[1]) { ju = 0; ++ku; }
       }
+    }
+    ch += dch;
+    j += dj;
+    k += dk;
+    if (ch >= nch) { ch -= nch; ++j; }
+    if (j >= L.n[1]) { j -= L.n[1]; ++k; }
+    {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (ib + lane + 32 * u >= L.n[0]) continue;
+        if (!live[u]) continue;
         const ST rho = q[u][0], ri = ST(1) / rho;
         const ST uu = q[u][1] * ri, vv = q[u][2] * ri, ww = q[u][3] * ri;
         const ST p = gm1 * (q[u][4] - ST(0.5) * rho * (uu * uu + vv * vv + ww * ww));

@@ -48,6 +48,7 @@ def test_paper_scale_footprint(L):
     (lambda d: d.update(bc=[0, 2, 2, 2, 2, 2]), "periodic"),
     (lambda d: d.update(bc=[9, 2, 2, 2, 2, 2]), "boundary kind"),
     (lambda d: d.update(hi=[0.0, 8.0, 8.0]), "extent"),
+    (lambda d: d.update(ni=64, nj=1 << 15, nk=1 << 15), "too large"),  # 2^31 rows of 32 nodes
 ])
 def test_bad_descriptors_rejected(L, mutate, msg):
     d = W.jet_grid(16, 16, 16)
@@ -116,3 +117,10 @@ def test_serving_selection_is_oldest_first_until_filled():
     two = serve.select_cases(resident, pts[3] + 1)
     assert [c["req"].rid for c in two] == [3, 1]
     assert [c["req"].rid for c in serve.select_cases(resident, 10**9)] == [3, 1, 2, 0]
+
+
+
+def test_largest_row_count_accepted(L):
+    """Just below the 32-bit row limit the descriptor is valid (sizing only)."""
+    d = dict(W.jet_grid(16, 16, 16), ni=32, nj=1 << 15, nk=1 << 15)
+    assert jz.jz_grid_bytes(d) > 0

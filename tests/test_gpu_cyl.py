@@ -173,3 +173,51 @@ def test_cylinder_with_vreman_and_fp64_state(jz, orc):
     for v in range(5):
         e = np.abs(got[v][sel] - ref[v][sel]).max() / np.abs(ref[v]).max()
         assert e <= (2e-3 if v in (2, 3) else 5e-5), (v, e)
+
+
+def seq_mean(ring):
+    """The mean of one azimuthal ring summed in azimuthal order in FP64."""
+    s = 0.0
+    for x in ring:
+        s += float(x)
+    return s / len(ring)
+
+
+def check_centreline_sequential(Q, grid, prec):
+    P = grid["nk"] - 1
+    for v in range(5):
+        for i in range(1, grid["ni"] - 1):  # the x faces own their centreline nodes
+            m = seq_mean(Q[v, :P, 1, i])
+            want = float(np.float32(m)) if prec != W.P64 else m
+            assert np.all(Q[v, :, 0, i] == want), (v, i)
+
+
+@pytest.mark.parametrize("prec", [W.P64, W.P32])
+def test_centreline_is_the_sequential_fp64_mean(jz, prec):
+    """Section 4.3: the centreline average is formed sequentially so that a
+    parallel run reproduces the serial one bit for bit.  Every centreline
+    node away from the x faces must be bitwise the FP64 mean of its j = 1
+    ring summed in azimuthal order, rounded to the state's type: after steps
+    of the jet, and for uploaded rings that force the FP32 kernel off its
+    exact integer sum (values 2^40 apart, a NaN-free ring with exact
+    cancellation, all-zero rings, subnormal FP32 values)."""
+    grid = W.cyl_grid(20, 10, 65, precision=prec)
+    g = jz.Grid(grid).init(W.jet_flow(re=2e4), 3)
+    g.nsteps(3, cfl=0.5)
+    Q = g.download()
+    check_centreline_sequential(Q, grid, prec)
+    rng = np.random.default_rng(11)
+    P = grid["nk"] - 1
+    Q = Q.copy()
+    ring = Q[1, :P, 1, 4]
+    ring[:] = rng.uniform(0.5, 1.5, P)
+    ring[::7] = 1e-12 * rng.uniform(1, 2, ring[::7].size)  # unit in the last place far below the sum: rounding
+    Q[2, :P, 1, 5] = np.where(np.arange(P) % 2 == 0, 0.75, -0.75)  # exact cancellation
+    Q[3, :P, 1, 6] = 0.0
+    Q[2, :P, 1, 7] = 1e-40 * rng.uniform(-1, 1, P)  # subnormal in FP32
+    Q[3, :P, 1, 8] = rng.uniform(-1, 1, P) * 2.0 ** rng.integers(-30, 30, P)  # wide exponent spread
+    Q[:, P] = Q[:, 0]
+    g.upload(Q)
+    got = g.download()
+    check_centreline_sequential(got, grid, prec)
+    g.close()
