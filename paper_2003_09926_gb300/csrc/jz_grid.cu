@@ -398,11 +398,12 @@ __global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constan
 // mean of Q_v over the P distinct azimuthal nodes of the radial line j = 1,
 // summed in azimuthal order in FP64 -- the sequential order the paper keeps
 // so that a partitioned run reproduces the serial one bit for bit.
-// A block takes 32 consecutive i of one variable (blockIdx.y).  The loads
-// are issued in parallel: the azimuth goes through shared memory in chunks
-// of 24 KB (192 FP32 or 96 FP64 values per i), seven warps loading the next
-// chunk (one coalesced row of 32 i per load) while warp 0 adds the current
-// one, lane = i, value by value in azimuthal order.
+// A block takes 32 consecutive i of one variable (blockIdx.y); lane = i.
+// This is the general form, used for FP64 states: the loads are issued in
+// parallel, the azimuth going through shared memory in chunks of 24 KB (96
+// FP64 values per i), seven warps loading the next chunk (one coalesced row
+// of 32 i per load) while warp 0 adds the current one value by value in
+// azimuthal order.  FP32 states take axis_mean_f32 below.
 constexpr int AX_WARPS = 8;
 constexpr int AX_BYTES = 24576;  // one chunk buffer; two are used
 
