@@ -526,6 +526,11 @@ int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
   F.ic = f->ic;
   F.sgs = f->sgs;
   F.viscous = (F.mu_inf > 0.0 || F.cs > 0.0) ? 1 : 0;
+  F.vfac = std::fmax(4.0 / 3.0, f->gamma / f->pr);
+  F.gamma_f = (float)F.gamma;
+  F.gm1_f = (float)F.gm1;
+  F.pe_f = (float)(1.0 / F.gamma);
+  F.vfac_f = (float)F.vfac;
   if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
   if (g->graph) { cudaGraphDestroy(g->graph); g->graph = nullptr; }
   g->graph_cfl = g->graph_dt = -1.0;

@@ -64,7 +64,23 @@ struct FlowC {
   int ic;
   int sgs;      // JZ_SGS_SMAGORINSKY or JZ_SGS_VREMAN
   int viscous;  // mu_inf > 0 or cs > 0
+  // the viscous rate factor max(4/3, gamma/Pr), and FP32 roundings of the
+  // constants the FP32 boundary fill and reductions use per node (formed on
+  // the host: GB300's FP64 pipe is narrow, and a conversion or division on
+  // it per node dominated the FP32 fill)
+  double vfac;
+  float gamma_f, gm1_f, pe_f, vfac_f;  // gamma, gamma - 1, 1/gamma, vfac
 };
+
+// a flow constant in the arithmetic type T: the FP64 value, or its FP32
+// rounding formed on the host
+template <typename T>
+__device__ __forceinline__ T flow_const(double d, float f) {
+  if constexpr (sizeof(T) == 4)
+    return f;
+  else
+    return (T)d;
+}
 
 // 1-D coordinate tables (FP64), indexed by node index + NG:
 //   box: x_d(i,j,k) = base[d][i_d] + amp * h[d][i_d] * sn[d][0][i] * sn[d][1][j] * sn[d][2][k]

@@ -207,7 +207,7 @@ __device__ __forceinline__ double jet_profile(const FlowC& F, double r) {
 // copies the upwind state.
 template <typename T>
 __device__ void riemann_farfield(const FlowC& F, const T qi[5], const T n[3], T qb[5]) {
-  const T g = (T)F.gamma, gm1 = (T)F.gm1;
+  const T g = flow_const<T>(F.gamma, F.gamma_f), gm1 = flow_const<T>(F.gm1, F.gm1_f);
   T rho_i = qi[0];
   T ri = T(1) / rho_i;
   T u[3] = {qi[1] * ri, qi[2] * ri, qi[3] * ri};
@@ -369,7 +369,8 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c] = qv[u][c];
       } else if (kind[u] == 1) {
-        to_conserved<ST>((ST)F.gm1, ST(1), (ST)uin[u], ST(0), ST(0), (ST)(1.0 / F.gamma), v);
+        to_conserved<ST>(flow_const<ST>(F.gm1, F.gm1_f), ST(1), (ST)uin[u], ST(0), ST(0),
+                         flow_const<ST>(1.0 / F.gamma, F.pe_f), v);
       } else if (kind[u] == 3) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c] = (ST)axis[c * L.n[0] + inf[u]];

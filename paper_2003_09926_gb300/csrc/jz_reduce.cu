@@ -54,9 +54,9 @@ template <typename ST, typename MT>
 __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, const ST* __restrict__ Q,
                                               const MT* __restrict__ M, Scalars* sc, double* partial, double cfl,
                                               bool finalize = true) {
-  const ST g = (ST)F.gamma, gm1 = (ST)F.gm1;
+  const ST g = flow_const<ST>(F.gamma, F.gamma_f), gm1 = flow_const<ST>(F.gm1, F.gm1_f);
   const ST mu_inf = (ST)F.mu_inf, s1 = (ST)F.s1;
-  const ST vfac = (ST)fmax(4.0 / 3.0, F.gamma / F.pr);
+  const ST vfac = flow_const<ST>(F.vfac, F.vfac_f);
   // the maximum is taken in the arithmetic type: exact, and the same value
   // as a maximum of the widened rates
   ST best_s = ST(0);
@@ -209,7 +209,7 @@ __global__ void k_fixed_dt(Scalars* sc, double dt) {
 template <typename ST, typename MT>
 __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const ST* __restrict__ Q,
                                                       const MT* __restrict__ M, Scalars* sc, double* partial) {
-  const ST gm1 = (ST)F.gm1, g = (ST)F.gamma;
+  const ST gm1 = flow_const<ST>(F.gm1, F.gm1_f), g = flow_const<ST>(F.gamma, F.gamma_f);
   RunSum<ST> sum[5];
   ST rmin = ST(INFINITY), rmax = ST(-INFINITY), pmin = ST(INFINITY), pmax = ST(-INFINITY), m2max = ST(0);
   double nonfinite = 0.0;
