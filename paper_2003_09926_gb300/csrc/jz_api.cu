@@ -497,6 +497,18 @@ int jz_grid_destroy(jz_grid* g) {
   return JZ_OK;
 }
 
+// After a new state: the boundary pass over both ghost layers, then the
+// whole padded arrays of Q^n copied into the two stage buffers, so that the
+// second ghost layer behind physical faces, which the per-stage passes leave
+// alone, holds finite values in every buffer (no updated node depends on it).
+static int set_state_ghosts(jz_grid* g) {
+  JZ_CUDA(launch_bc(g->dev, g->dev.Q0, g->stream, true));
+  const size_t bytes = 5 * (size_t)g->dev.L.npad * (g->dev.prec == JZ_P64 ? 8 : 4);
+  JZ_CUDA(cudaMemcpyAsync(g->dev.QA, g->dev.Q0, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  JZ_CUDA(cudaMemcpyAsync(g->dev.QB, g->dev.Q0, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  return JZ_OK;
+}
+
 int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
   if (int rc = check_grid(g, false)) return rc;
   if (!f) return fail(JZ_EINVAL, "null flow parameters");
@@ -536,8 +548,7 @@ int jz_state_init(jz_grid* g, const jz_flow_params* f, uint64_t seed) {
   g->graph_cfl = g->graph_dt = -1.0;
   JZ_CUDA(cudaMemsetAsync(g->dev.sc, 0, sizeof(Scalars), g->stream));
   JZ_CUDA(launch_init(g->dev, seed, g->stream));
-  JZ_CUDA(launch_bc(g->dev, g->dev.Q0, g->stream));
-  return JZ_OK;
+  return set_state_ghosts(g);
 }
 
 int jz_rk_step(jz_grid* g, double cfl, double dt_fixed) {
@@ -638,7 +649,7 @@ int jz_state_upload(jz_grid* g, const double* host, size_t n) {
   double* staging = (double*)g->dev.QA;
   JZ_CUDA(cudaMemcpyAsync(staging, host, n * sizeof(double), cudaMemcpyHostToDevice, g->stream));
   JZ_CUDA(launch_unpack(g->dev, staging, g->stream));
-  JZ_CUDA(launch_bc(g->dev, g->dev.Q0, g->stream));
+  if (int rc = set_state_ghosts(g)) return rc;
   JZ_CUDA(cudaStreamSynchronize(g->stream));
   return JZ_OK;
 }

@@ -748,9 +748,22 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s) {
 }
 
 // the padded nodes outside the updated box [lo, hi]
-Slabs bc_slabs(const Layout& L) {
-  const int pad_lo[3] = {-NG, -NG, -NG};
-  const int pad_hi[3] = {L.n[0] + 1, L.n[1] + 1, L.n[2] + 1};
+// The padded nodes a boundary pass sets.  Behind a physical face (inflow,
+// far field, centreline) the stages read one ghost layer only: the first
+// updated node is one in from the boundary node, so its five-point stencil
+// reaches one node past it, and the second layer enters nothing but the
+// residual of the boundary node, which is not updated.  The per-stage pass
+// (full = false) therefore sets the boundary nodes and the first ghost
+// layer there; periodic directions and exchange faces keep both layers.  The
+// pass after a state is set (full = true) covers both layers everywhere.
+Slabs bc_slabs(const Layout& L, bool full) {
+  int pad_lo[3], pad_hi[3];
+  for (int a = 0; a < 3; ++a) {
+    const bool keep_lo = full || L.bc[2 * a] == BC_PERIODIC || L.bc[2 * a] == BC_EXCHANGE;
+    const bool keep_hi = full || L.bc[2 * a + 1] == BC_PERIODIC || L.bc[2 * a + 1] == BC_EXCHANGE;
+    pad_lo[a] = keep_lo ? -NG : -1;
+    pad_hi[a] = keep_hi ? L.n[a] + 1 : L.n[a];
+  }
   return make_slabs(pad_lo, pad_hi, L.lo, L.hi);
 }
 
@@ -767,8 +780,8 @@ int slab_blocks(const Slabs& sl) {
   return b < 128 ? b : 128;
 }
 
-cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s) {
-  const Slabs sl = bc_slabs(g.L);
+cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s, bool full) {
+  const Slabs sl = bc_slabs(g.L, full);
   const dim3 b(slab_blocks(sl), 6);
   if (g.L.cyl) {
     const dim3 ab((g.L.n[0] + 31) / 32, 5);
@@ -799,7 +812,7 @@ size_t bc_ctx_bytes() { return sizeof(BcCtx); }
 void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
   BcCtx& X = *(BcCtx*)dst;
   X.L = g.L;
-  X.fill = bc_slabs(g.L);
+  X.fill = bc_slabs(g.L, false);
   X.inflow = g.inflow;
   X.axis = g.axis;
   X.F = g.F;

@@ -60,7 +60,7 @@ int record_error(int code, const char* msg);
 cudaError_t launch_tables(const TabParams& p, double* tables, cudaStream_t s);
 cudaError_t launch_metrics(const GridDev& g, cudaStream_t s);
 cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s);
-cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s);
+cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s, bool full = false);
 cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s);
 cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
 
