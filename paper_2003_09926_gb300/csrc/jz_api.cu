@@ -201,8 +201,8 @@ struct jz_batch {
   cudaStream_t stream = nullptr;
   int prec = 0;
   char* dev = nullptr;
-  size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0;
-  int nitems = 0, bc_blocks = 1;
+  size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0, off_bcitems = 0;
+  int nitems = 0, nbcitems = 0;
   bool cyl = false;             // some grid is cylindrical (centreline means before each boundary pass)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -736,8 +736,9 @@ int jz_set_tiling(jz_grid* g, int kc) {
 namespace {
 
 struct BatchPlan {
-  size_t off_stage, off_bc, off_rate, off_items, off_queue, off_x, total;
+  size_t off_stage, off_bc, off_rate, off_items, off_queue, off_x, off_bcitems, total;
   std::vector<int4> items;
+  std::vector<int4> bcitems;  // boundary-pass work items
   std::vector<XEntry> xs;  // halo exchange (blocks of one grid)
   int xbegin[3] = {0, 0, 0}, xcount[3] = {0, 0, 0}, xblocks = 1;
 };
@@ -785,6 +786,9 @@ int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
   P.off_items = off; off = align256(off + P.items.size() * sizeof(int4));
   P.off_queue = off; off = align256(off + sizeof(unsigned int));
   P.off_x = off; off = align256(off + P.xs.size() * sizeof(XEntry));
+  P.bcitems.clear();
+  for (int k = 0; k < n; ++k) bc_fill_items(grids[k]->dev, k, P.bcitems);
+  P.off_bcitems = off; off = align256(off + P.bcitems.size() * sizeof(int4));
   P.total = off;
   return JZ_OK;
 }
@@ -876,7 +880,8 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
     e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, grid_tiling(b->grids[0]->dev), b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
                            (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
-    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, b->bc_blocks, out[l], b->cyl, s);
+    e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, (const int4*)(b->dev + b->off_bcitems), b->nbcitems, out[l],
+                        b->cyl, s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched boundary launch failed: %s", cudaGetErrorString(e));
     if (b->coupled && l < 4)
       if (int rc = enqueue_exchange(b, out[l])) return rc;
@@ -895,16 +900,14 @@ int create_batch(jz_grid* const* grids, int n, bool coupled, void* dev_buf, size
   if (bytes < P.total) return fail(JZ_ENOMEM, "batch buffer holds %zu bytes, batch needs %zu", bytes, P.total);
   const int prec = grids[0]->dev.prec;
   std::vector<char> host(P.total, 0);
-  int nb = 1;
   for (int k = 0; k < n; ++k) {
     stage_ctx_fill(host.data() + P.off_stage + (size_t)k * stage_ctx_bytes(prec), grids[k]->dev);
-    int a = 1;
-    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev, &a);
-    nb = std::max(nb, a);
+    bc_ctx_fill(host.data() + P.off_bc + (size_t)k * bc_ctx_bytes(), grids[k]->dev);
     rate_ctx_fill(host.data() + P.off_rate + (size_t)k * rate_ctx_bytes(), grids[k]->dev);
   }
   memcpy(host.data() + P.off_items, P.items.data(), P.items.size() * sizeof(int4));
   if (!P.xs.empty()) memcpy(host.data() + P.off_x, P.xs.data(), P.xs.size() * sizeof(XEntry));
+  memcpy(host.data() + P.off_bcitems, P.bcitems.data(), P.bcitems.size() * sizeof(int4));
   JZ_CUDA(cudaMemcpy(dev_buf, host.data(), P.total, cudaMemcpyHostToDevice));
   jz_batch* b = new (std::nothrow) jz_batch();
   if (!b) return fail(JZ_ENOMEM, "host allocation failed");
@@ -918,10 +921,8 @@ int create_batch(jz_grid* const* grids, int n, bool coupled, void* dev_buf, size
   b->off_items = P.off_items;
   b->off_queue = P.off_queue;
   b->nitems = (int)P.items.size();
-  // blocks per slab and grid of the batched fill: at most 32 (64 uneven grids:
-  // 13.39 ms per batch step against 13.61 ms with up to 128; most grids' slabs
-  // are small, and idle blocks still cost their scheduling)
-  b->bc_blocks = std::min(nb, 32);
+  b->off_bcitems = P.off_bcitems;
+  b->nbcitems = (int)P.bcitems.size();
   for (int k = 0; k < n; ++k) b->cyl = b->cyl || grids[k]->dev.L.cyl;
   b->coupled = coupled;
   b->off_x = P.off_x;

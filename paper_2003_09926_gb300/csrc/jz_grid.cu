@@ -6,7 +6,9 @@
 // Section 4.2 (Jacobian and metric terms computed once after the mesh is
 // read; boundary update at the start of every Runge-Kutta stage) and
 // Section 4.3 (two-layer ghost fringe).
+#include <algorithm>
 #include <climits>
+#include <vector>
 #include <cmath>
 
 #include "jz_internal.h"
@@ -282,15 +284,16 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
 // launch, and every node gets the value of a boundary pass followed by a
 // ghost copy.
 template <typename ST, typename MT>
-__device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, const double* inflow,
+__device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, int t_begin, int t_step, int t_end,
+                                          const double* inflow,
                                           const double* axis, const FlowC& F, ST* __restrict__ Q,
                                           const MT* __restrict__ M) {
   // one node per thread (four per thread with their loads issued together
   // measured slower: fewer resident threads)
   constexpr int U = 1;
-  const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
-  const int bw = blockDim.x;
-  for (int tb = blockIdx.x * bw * U + threadIdx.x; tb < tot; tb += gridDim.x * bw * U) {
+  const int tot = min(t_end, sl.e[q][0] * sl.e[q][1] * sl.e[q][2]);
+  const int bw = t_step;
+  for (int tb = t_begin; tb < tot; tb += t_step * U) {
     long long dst[U], src[U], nb[U];
     int kind[U], face[U], inf[U];  // kind: 0 copy, 1 inflow, 2 far field, 3 centreline, -1 none
 #pragma unroll
@@ -391,7 +394,8 @@ template <typename ST, typename MT>
 __global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constant__ Slabs sl,
                           const double* __restrict__ inflow, const double* __restrict__ axis,
                           const __grid_constant__ FlowC F, ST* __restrict__ Q, const MT* __restrict__ M) {
-  fill_slab<ST, MT>(L, sl, blockIdx.y, inflow, axis, F, Q, M);
+  fill_slab<ST, MT>(L, sl, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, INT_MAX, inflow,
+                    axis, F, Q, M);
 }
 
 // Centreline of a cylindrical grid (the paper's singularity treatment,
@@ -559,10 +563,15 @@ struct BcCtx {
   const void* M;
 };
 
+// one work item per block: (grid, slab, first node, end node) of the slab's
+// enumeration, at most BC_ITEM_NODES nodes, so that the blocks follow the
+// slab sizes of uneven grids
 template <typename ST, typename MT>
-__global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, int which) {
-  const BcCtx& X = ctx[blockIdx.z];
-  fill_slab<ST, MT>(X.L, X.fill, blockIdx.y, X.inflow, X.axis, X.F, (ST*)X.Q[which], (const MT*)X.M);
+__global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, const int4* __restrict__ items, int which) {
+  const int4 w = items[blockIdx.x];
+  const BcCtx& X = ctx[w.x];
+  fill_slab<ST, MT>(X.L, X.fill, w.y, w.z + threadIdx.x, blockDim.x, w.w, X.inflow, X.axis, X.F, (ST*)X.Q[which],
+                    (const MT*)X.M);
 }
 
 template <typename ST>
@@ -808,8 +817,8 @@ cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s, bool full) {
 
 size_t bc_ctx_bytes() { return sizeof(BcCtx); }
 
-// fills the host-side table entry; returns the block count the fill needs
-void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
+// fills the host-side table entry
+void bc_ctx_fill(void* dst, const GridDev& g) {
   BcCtx& X = *(BcCtx*)dst;
   X.L = g.L;
   X.fill = bc_slabs(g.L, false);
@@ -820,11 +829,18 @@ void bc_ctx_fill(void* dst, const GridDev& g, int* blocks) {
   X.Q[1] = g.QA;
   X.Q[2] = g.QB;
   X.M = g.M;
-  *blocks = slab_blocks(X.fill);
 }
 
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, bool cyl, cudaStream_t s) {
-  const dim3 b(blocks, 6, n);
+void bc_fill_items(const GridDev& g, int grid, std::vector<int4>& out) {
+  const Slabs sl = bc_slabs(g.L, false);
+  for (int q = 0; q < 6; ++q) {
+    const int tot = sl.e[q][0] * sl.e[q][1] * sl.e[q][2];
+    for (int t = 0; t < tot; t += BC_ITEM_NODES) out.push_back(make_int4(grid, q, t, std::min(tot, t + BC_ITEM_NODES)));
+  }
+}
+
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, const int4* items, int nitems, int which, bool cyl,
+                            cudaStream_t s) {
   const BcCtx* X = (const BcCtx*)ctx;
   if (cyl) {  // some grid of the batch is cylindrical: centreline means first
     const dim3 ab(8, 5, n);
@@ -835,9 +851,9 @@ cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int wh
     count_launches(1);
   }
   switch (prec) {
-    case JZ_P64: k_bc_fill_batch<double, double><<<b, 256, 0, s>>>(X, which); break;
-    case JZ_P32_M64: k_bc_fill_batch<float, double><<<b, 256, 0, s>>>(X, which); break;
-    default: k_bc_fill_batch<float, float><<<b, 256, 0, s>>>(X, which); break;
+    case JZ_P64: k_bc_fill_batch<double, double><<<nitems, 256, 0, s>>>(X, items, which); break;
+    case JZ_P32_M64: k_bc_fill_batch<float, double><<<nitems, 256, 0, s>>>(X, items, which); break;
+    default: k_bc_fill_batch<float, float><<<nitems, 256, 0, s>>>(X, items, which); break;
   }
   count_launches(1);
   return cudaGetLastError();

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -66,8 +67,13 @@ cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
 
 // batched boundary fill over a device table of per-grid contexts
 size_t bc_ctx_bytes();
-void bc_ctx_fill(void* host_dst, const GridDev& g, int* blocks);
-cudaError_t launch_bc_batch(int prec, const void* ctx, int n, int blocks, int which, bool cyl, cudaStream_t s);
+void bc_ctx_fill(void* host_dst, const GridDev& g);
+// batched boundary pass: work items (grid, slab, first node, end node) of at
+// most BC_ITEM_NODES nodes (one 256-thread block each)
+constexpr int BC_ITEM_NODES = 1024;
+void bc_fill_items(const GridDev& g, int grid, std::vector<int4>& out);
+cudaError_t launch_bc_batch(int prec, const void* ctx, int n, const int4* items, int nitems, int which, bool cyl,
+                            cudaStream_t s);
 
 // halo exchange between blocks of one grid: one entry per (block, exchange face)
 struct XEntry {
