@@ -11,6 +11,7 @@
 #include <vector>
 #include <cmath>
 
+#include "jz_fastmath.cuh"
 #include "jz_internal.h"
 
 namespace jz {
@@ -190,13 +191,28 @@ __global__ void k_fill_ghosts(Layout L, Shell s, T* __restrict__ F, int ncomp) {
 // gas model helpers (Eq. 2, equation of state)
 // ---------------------------------------------------------------------------
 
-template <typename T>
+// Elementary operations of the boundary formulas: IEEE, or (FAST, FP32
+// states of the P32 and P32_M64 modes) the hardware approximations of the
+// stage kernels.  The P32_S64 mode keeps IEEE operations: its boundary
+// values enter the FP64 state of the neighbouring nodes every stage, and an
+// approximation's bias of an ulp there measurably raised its long-run error.
+template <typename T, bool FAST>
+struct BcMath {
+  static __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+  static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+  static __device__ __forceinline__ T sqrt_(T x) { return sqrt(x); }
+  static __device__ __forceinline__ T powp(T x, T e) { return pow(x, e); }
+};
+template <>
+struct BcMath<float, true> : stg::Fn<float> {};
+
+template <typename T, bool FAST = false>
 __device__ __forceinline__ void to_conserved(T gm1, T rho, T u, T v, T w, T p, T q[5]) {
   q[0] = rho;
   q[1] = rho * u;
   q[2] = rho * v;
   q[3] = rho * w;
-  q[4] = p / gm1 + T(0.5) * rho * (u * u + v * v + w * w);
+  q[4] = BcMath<T, FAST>::div(p, gm1) + T(0.5) * rho * (u * u + v * v + w * w);
 }
 
 __device__ __forceinline__ double jet_profile(const FlowC& F, double r) {
@@ -207,39 +223,40 @@ __device__ __forceinline__ double jet_profile(const FlowC& F, double r) {
 // R+ = u_n + 2c/(g-1) from the interior, R- = -2/(g-1) from outside; entropy
 // and tangential velocity from the upwind side; supersonic normal speed
 // copies the upwind state.
-template <typename T>
+template <typename T, bool FAST>
 __device__ void riemann_farfield(const FlowC& F, const T qi[5], const T n[3], T qb[5]) {
+  using M = BcMath<T, FAST>;
   const T g = flow_const<T>(F.gamma, F.gamma_f), gm1 = flow_const<T>(F.gm1, F.gm1_f);
   T rho_i = qi[0];
-  T ri = T(1) / rho_i;
+  T ri = M::rcp(rho_i);
   T u[3] = {qi[1] * ri, qi[2] * ri, qi[3] * ri};
   T p_i = gm1 * (qi[4] - T(0.5) * rho_i * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-  T c_i = sqrt(g * p_i * ri);
+  T c_i = M::sqrt_(g * p_i * ri);
   T un_i = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
   if (un_i >= c_i) {
     for (int v = 0; v < 5; ++v) qb[v] = qi[v];
     return;
   }
-  const T p_e = T(1) / g;
+  const T p_e = M::rcp(g);
   if (un_i <= -c_i) {
-    to_conserved<T>(gm1, T(1), T(0), T(0), T(0), p_e, qb);
+    to_conserved<T, FAST>(gm1, T(1), T(0), T(0), T(0), p_e, qb);
     return;
   }
-  T Rp = un_i + T(2) * c_i / gm1;
-  T Rm = -T(2) / gm1;  // exterior u_n = 0, c = 1
+  T Rp = un_i + M::div(T(2) * c_i, gm1);
+  T Rm = M::div(-T(2), gm1);  // exterior u_n = 0, c = 1
   T un = T(0.5) * (Rp + Rm);
   T c = T(0.25) * gm1 * (Rp - Rm);
   T s, ut[3];
   if (un > T(0)) {
-    s = p_i / pow(rho_i, g);
+    s = M::div(p_i, M::powp(rho_i, g));
     for (int d = 0; d < 3; ++d) ut[d] = u[d] - un_i * n[d];
   } else {
     s = p_e;  // p_e / rho_e^g with rho_e = 1
     for (int d = 0; d < 3; ++d) ut[d] = T(0);
   }
-  T rho = pow(c * c / (g * s), T(1) / gm1);
-  T p = rho * c * c / g;
-  to_conserved<T>(gm1, rho, ut[0] + un * n[0], ut[1] + un * n[1], ut[2] + un * n[2], p, qb);
+  T rho = M::powp(M::div(c * c, g * s), M::rcp(gm1));
+  T p = M::div(rho * c * c, g);
+  to_conserved<T, FAST>(gm1, rho, ut[0] + un * n[0], ut[1] + un * n[1], ut[2] + un * n[2], p, qb);
 }
 
 // Six boxes covering the padded nodes that lie inside an outer box [ol, oh]
@@ -283,7 +300,7 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
 // node.  Only updated nodes are read, so the pass is race-free in one
 // launch, and every node gets the value of a boundary pass followed by a
 // ghost copy.
-template <typename ST, typename MT>
+template <typename ST, typename MT, bool FAST>
 __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int q, int t_begin, int t_step, int t_end,
                                           const double* inflow,
                                           const double* axis, const FlowC& F, ST* __restrict__ Q,
@@ -372,17 +389,17 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c] = qv[u][c];
       } else if (kind[u] == 1) {
-        to_conserved<ST>(flow_const<ST>(F.gm1, F.gm1_f), ST(1), (ST)uin[u], ST(0), ST(0),
-                         flow_const<ST>(1.0 / F.gamma, F.pe_f), v);
+        to_conserved<ST, FAST>(flow_const<ST>(F.gm1, F.gm1_f), ST(1), (ST)uin[u], ST(0), ST(0),
+                               flow_const<ST>(1.0 / F.gamma, F.pe_f), v);
       } else if (kind[u] == 3) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) v[c] = (ST)axis[c * L.n[0] + inf[u]];
       } else {
         const ST a = mv[u][0], b = mv[u][1], cc = mv[u][2];
         const ST sgn = (face[u] % 2 == 0) ? ST(-1) : ST(1);
-        const ST inv = sgn / sqrt(a * a + b * b + cc * cc);
+        const ST inv = BcMath<ST, FAST>::div(sgn, BcMath<ST, FAST>::sqrt_(a * a + b * b + cc * cc));
         const ST n[3] = {a * inv, b * inv, cc * inv};
-        riemann_farfield<ST>(F, qv[u], n, v);
+        riemann_farfield<ST, FAST>(F, qv[u], n, v);
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) Q[(long long)c * L.npad + dst[u]] = v[c];
@@ -390,11 +407,11 @@ __device__ __forceinline__ void fill_slab(const Layout& L, const Slabs& sl, int 
   }
 }
 
-template <typename ST, typename MT>
+template <typename ST, typename MT, bool FAST>
 __global__ void k_bc_fill(const __grid_constant__ Layout L, const __grid_constant__ Slabs sl,
                           const double* __restrict__ inflow, const double* __restrict__ axis,
                           const __grid_constant__ FlowC F, ST* __restrict__ Q, const MT* __restrict__ M) {
-  fill_slab<ST, MT>(L, sl, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, INT_MAX, inflow,
+  fill_slab<ST, MT, FAST>(L, sl, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, INT_MAX, inflow,
                     axis, F, Q, M);
 }
 
@@ -566,11 +583,11 @@ struct BcCtx {
 // one work item per block: (grid, slab, first node, end node) of the slab's
 // enumeration, at most BC_ITEM_NODES nodes, so that the blocks follow the
 // slab sizes of uneven grids
-template <typename ST, typename MT>
+template <typename ST, typename MT, bool FAST>
 __global__ void k_bc_fill_batch(const BcCtx* __restrict__ ctx, const int4* __restrict__ items, int which) {
   const int4 w = items[blockIdx.x];
   const BcCtx& X = ctx[w.x];
-  fill_slab<ST, MT>(X.L, X.fill, w.y, w.z + threadIdx.x, blockDim.x, w.w, X.inflow, X.axis, X.F, (ST*)X.Q[which],
+  fill_slab<ST, MT, FAST>(X.L, X.fill, w.y, w.z + threadIdx.x, blockDim.x, w.w, X.inflow, X.axis, X.F, (ST*)X.Q[which],
                     (const MT*)X.M);
 }
 
@@ -802,13 +819,17 @@ cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s, bool full) {
   }
   switch (g.prec) {
     case JZ_P64:
-      k_bc_fill<double, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (double*)Q, (const double*)g.M);
+      k_bc_fill<double, double, false><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (double*)Q,
+                                                         (const double*)g.M);
       break;
     case JZ_P32_M64:
-      k_bc_fill<float, double><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const double*)g.M);
+      k_bc_fill<float, double, true><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const double*)g.M);
+      break;
+    case JZ_P32_S64:
+      k_bc_fill<float, float, false><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const float*)g.M);
       break;
     default:
-      k_bc_fill<float, float><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const float*)g.M);
+      k_bc_fill<float, float, true><<<b, 256, 0, s>>>(g.L, sl, g.inflow, g.axis, g.F, (float*)Q, (const float*)g.M);
       break;
   }
   count_launches(1);
@@ -851,9 +872,10 @@ cudaError_t launch_bc_batch(int prec, const void* ctx, int n, const int4* items,
     count_launches(1);
   }
   switch (prec) {
-    case JZ_P64: k_bc_fill_batch<double, double><<<nitems, 256, 0, s>>>(X, items, which); break;
-    case JZ_P32_M64: k_bc_fill_batch<float, double><<<nitems, 256, 0, s>>>(X, items, which); break;
-    default: k_bc_fill_batch<float, float><<<nitems, 256, 0, s>>>(X, items, which); break;
+    case JZ_P64: k_bc_fill_batch<double, double, false><<<nitems, 256, 0, s>>>(X, items, which); break;
+    case JZ_P32_M64: k_bc_fill_batch<float, double, true><<<nitems, 256, 0, s>>>(X, items, which); break;
+    case JZ_P32_S64: k_bc_fill_batch<float, float, false><<<nitems, 256, 0, s>>>(X, items, which); break;
+    default: k_bc_fill_batch<float, float, true><<<nitems, 256, 0, s>>>(X, items, which); break;
   }
   count_launches(1);
   return cudaGetLastError();
