@@ -64,7 +64,11 @@ extern "C" {
 #define JZ_GEOM_BOX 0      /* Cartesian box, optional tanh clustering and mapping */
 #define JZ_GEOM_CYLINDER 1 /* the paper's cylindrical jet grid (Section 3)        */
 
-/* precision modes: state/flux arithmetic, metric storage */
+/* precision modes: state/flux arithmetic, metric storage.  FP32 flux
+ * arithmetic uses the hardware approximations of sqrt, reciprocal and
+ * powers (a few ulp); so do the boundary formulas of JZ_P32 and JZ_P32_M64,
+ * while JZ_P32_S64 evaluates them with IEEE FP32 operations.  JZ_P32 and
+ * JZ_P32_M64 give bitwise equal states with the scalar stage kernel. */
 #define JZ_P64 0     /* FP64 state and fluxes, FP64 metrics                   */
 #define JZ_P32_M64 1 /* FP32 state and fluxes, FP64-stored metrics             */
 #define JZ_P32 2     /* FP32 state and fluxes, FP64-generated FP32 metrics     */
@@ -120,7 +124,7 @@ typedef struct jz_grid_desc {
   double cluster_r, stretch_c, stretch_w;
   double map_amp;
   uint64_t map_seed;
-  int precision; /* JZ_P64, JZ_P32_M64 or JZ_P32 */
+  int precision; /* JZ_P64, JZ_P32_M64, JZ_P32 or JZ_P32_S64 */
   int geom;      /* JZ_GEOM_BOX or JZ_GEOM_CYLINDER */
 } jz_grid_desc;
 
