@@ -291,9 +291,11 @@ __device__ __forceinline__ bool slab_node(const Slabs& sl, int q, int t, int& i,
   return true;
 }
 
-// Boundary fill in one pass over the padded nodes outside the updated box:
-// each takes the value of the grid node its index maps to (wrap, clamp onto
-// the two ghost layers, or across the centreline of a cylindrical grid): a
+// Boundary fill in one pass over the padded nodes of the slabs (bc_slabs:
+// outside the updated box, one or two ghost layers deep), nodes [t_begin,
+// t_end) of slab q with stride t_step: each takes the value of the grid
+// node its index maps to (wrap, clamp for the ghost layers behind a face,
+// or across the centreline of a cylindrical grid): a
 // copy when that node is updated by the stages, its boundary-condition value
 // (computed here from the interior node it reads, or, on the centreline,
 // from the azimuthal means computed before this pass) when it is a boundary
