@@ -54,13 +54,15 @@ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 //   Vreman (2004): c Delta^2 sqrt(B / (g_am g_am)), c = 2.5 C_s^2, with
 //     b_ab = sum_m g[a][m] g[b][m] and B = b00 b11 - b01^2 + b00 b22 - b02^2
 //     + b11 b22 - b12^2 (the sum of b's principal 2x2 minors, >= 0; clamped at
-//     0 against rounding); 0 where all gradients vanish.  B <= (g_am g_am)^2/3,
-//     so the model tends to 0 with the gradients: below the smallest normal
-//     number (where the FP32 reciprocal flushes to zero) it is taken as 0.
+//     0 against rounding); 0 where all gradients vanish (g_am g_am = 0).
+//     B <= (g_am g_am)^2/3, so the model tends to 0 with the gradients.  In
+//     FP32 the reciprocal flushes subnormal operands to zero, so there the
+//     model is also taken as 0 where g_am g_am is below the smallest normal
+//     FP32 number; FP64 uses the plain > 0 test.
 template <typename R>
 __device__ __forceinline__ R eddy_nu(const KConst<R>& c, const R g[4][3], R Jn) {
   if (c.vreman) {
-    const R tiny = sizeof(R) == 4 ? R(1.17549435e-38f) : R(2.2250738585072014e-308);
+    const R tiny = sizeof(R) == 4 ? R(1.17549435e-38f) : R(0);
     R b[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)

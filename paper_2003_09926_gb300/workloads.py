@@ -119,35 +119,3 @@ def config4(nreq: int = 256, seed: int = 4, precision: int = P32, pts_lo: float 
         reqs.append(dict(grid=jet_grid(ni, nj, nj, precision=precision), flow=jet_flow(mach=mach, re=re),
                          seed=4000 + r, steps=steps))
     return dict(name="c4_serve", requests=reqs, cfl=0.5)
-
-
-# --- seeded synthetic states for tests ----------------------------------------
-
-def smooth_field(shape, rng, modes: int = 3, amp: float = 1.0):
-    """Sum of a few random periodic Fourier modes on an index-periodic box
-    (shape = (nk, nj, ni))."""
-    nk, nj, ni = shape
-    k, j, i = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
-    out = np.zeros(shape)
-    for _ in range(modes):
-        a, b, c = rng.integers(0, 3, size=3)
-        ph = rng.uniform(0, 2 * np.pi)
-        out += rng.uniform(-amp, amp) * np.cos(2 * np.pi * (a * i / ni + b * j / nj + c * k / nk) + ph)
-    return out
-
-
-def primitive_to_conserved(rho, u, v, w, p, gamma=1.4):
-    """Conserved vector [rho, rho u, rho v, rho w, p/(gamma-1) + rho |u|^2 / 2]."""
-    return np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)])
-
-
-def random_state(shape, seed: int, noise: float = 0.02, gamma: float = 1.4, mach: float = 1.4):
-    """Noisy jet-like state on an index-periodic box: smooth density,
-    pressure and velocity fields plus white noise.  Returns (5, nk, nj, ni)."""
-    rng = np.random.default_rng(seed)
-    rho = 1.0 + 0.1 * smooth_field(shape, rng) + noise * rng.uniform(-1, 1, shape)
-    p = (1.0 + 0.1 * smooth_field(shape, rng) + noise * rng.uniform(-1, 1, shape)) / gamma
-    u = mach * (0.5 + 0.3 * smooth_field(shape, rng)) + noise * rng.uniform(-1, 1, shape)
-    v = 0.2 * smooth_field(shape, rng) + noise * rng.uniform(-1, 1, shape)
-    w = 0.2 * smooth_field(shape, rng) + noise * rng.uniform(-1, 1, shape)
-    return primitive_to_conserved(rho, u, v, w, p, gamma)

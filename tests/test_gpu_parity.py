@@ -13,6 +13,8 @@ import pytest
 
 from paper_2003_09926_gb300 import workloads as W
 
+import states as ST
+
 pytestmark = pytest.mark.gpu
 
 NG = 2
@@ -94,7 +96,7 @@ def test_ragged_jet_grids_fp64(jz, orc, shape, amp):
 def test_periodic_mapped_viscous_fp64_conservation(jz, orc):
     grid = W.periodic_grid(34, 18, 12, hi=(2.0, 1.5, 1.2), map_amp=0.3, map_seed=5)
     flow = W.jet_flow(re=2e3, cs=0.18)
-    Qin = W.random_state((12, 18, 34), seed=7)
+    Qin = ST.random_state((12, 18, 34), seed=7)
     g, o, Q = run_pair(jz, orc, grid, flow, 0, 6, Qin=Qin)
     assert rel_err(g.download(), o.inner(Q)) <= 1e-10
     s1 = g.diagnostics()["sum"]
@@ -110,7 +112,7 @@ def test_one_node_periodic_direction_and_fixed_dt(jz, orc):
     grid = W.periodic_grid(40, 24, 1, lo=(-5, -3, 0), hi=(5, 3, 0.25), map_amp=0.1, map_seed=2)
     flow = W.jet_flow(re=0.0, cs=0.0)
     rng = np.random.default_rng(1)
-    Qin = W.random_state((1, 24, 40), seed=3, noise=0.0)
+    Qin = ST.random_state((1, 24, 40), seed=3, noise=0.0)
     g, o, Q = run_pair(jz, orc, grid, flow, 0, 5, cfl=0.0, dt=0.01, Qin=Qin)
     assert rel_err(g.download(), o.inner(Q)) <= 1e-10
     assert g.diagnostics()["dt"] == 0.01
@@ -123,7 +125,7 @@ def test_freestream_preservation(jz, prec, tol):
     g = jz.Grid(dict(grid, precision=prec)).init(W.jet_flow(re=1e3), 0)
     sh = (12, 20, 40)
     one = np.ones(sh)
-    Qin = W.primitive_to_conserved(one, 1.4 * np.cos(0.3) * one, 1.4 * np.sin(0.3) * one, 0.2 * one, one / 1.4)
+    Qin = ST.primitive_to_conserved(one, 1.4 * np.cos(0.3) * one, 1.4 * np.sin(0.3) * one, 0.2 * one, one / 1.4)
     g.upload(Qin)
     g.nsteps(20, cfl=0.5)
     got = g.download()
@@ -232,7 +234,7 @@ def test_sgs_model_is_validated(jz):
 
 def test_upload_download_roundtrip(jz):
     grid = W.jet_grid(20, 12, 10)
-    Qin = W.random_state((10, 12, 20), seed=1)
+    Qin = ST.random_state((10, 12, 20), seed=1)
     g = jz.Grid(grid).init(W.jet_flow(), 0)
     g.upload(Qin)
     got = g.download()
@@ -288,7 +290,7 @@ def test_fp32_kernel_variants_periodic(jz, variant, nk):
     kernel agrees with the scalar FP32 kernel to FP32 rounding after 5 steps
     at a fixed time step."""
     grid = W.periodic_grid(40, 20, nk, hi=(2.0, 1.5, 1.2), map_amp=0.3, map_seed=5, precision=W.P32)
-    Qin = W.random_state((nk, 20, 40), seed=7)
+    Qin = ST.random_state((nk, 20, 40), seed=7)
     outs = []
     for var in (variant, 0):
         g = jz.Grid(grid).init(W.jet_flow(re=2e3), 0)

@@ -10,6 +10,8 @@ import pytest
 
 from paper_2003_09926_gb300 import workloads as W
 
+import states as ST
+
 pytestmark = pytest.mark.gpu
 
 
@@ -58,7 +60,7 @@ def test_s64_updated_nodes_round_trip_in_fp64(jz):
     set by the boundary conditions in FP32."""
     grid = W.jet_grid(40, 24, 20, map_amp=0.03, map_seed=2, precision=W.P32_S64)
     g = jz.Grid(grid).init(W.jet_flow(), 0)
-    Qin = W.random_state((20, 24, 40), seed=4)
+    Qin = ST.random_state((20, 24, 40), seed=4)
     g.upload(Qin)
     got = g.download()
     inner = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))

@@ -15,6 +15,8 @@ import pytest
 
 from paper_2003_09926_gb300 import workloads as W
 
+import states as ST
+
 NG = 2
 
 
@@ -100,7 +102,7 @@ def test_cylinder_centreline_and_ghost_rules(orc):
     rng = np.random.default_rng(4)
     Q = o.new_state()
     Q[...] = np.nan
-    Q[:, NG:-NG, NG:-NG, NG:-NG] = W.random_state((nk, nj, ni), seed=9)
+    Q[:, NG:-NG, NG:-NG, NG:-NG] = ST.random_state((nk, nj, ni), seed=9)
     o.apply_bc(Q)
     for v in range(5):
         for i in range(1, ni - 1):
@@ -212,7 +214,7 @@ def test_cylinder_residual_converges_at_second_order(orc):
         o = orc.Oracle(d, W.jet_flow(re=0.0, cs=0.0, k2=0.0, k4=0.0))
         X = o.X
         one = np.ones_like(X[0])
-        Q = np.ascontiguousarray(W.primitive_to_conserved(*[fi(X[0], X[1], X[2]) * one for fi in f[:5]]))
+        Q = np.ascontiguousarray(ST.primitive_to_conserved(*[fi(X[0], X[1], X[2]) * one for fi in f[:5]]))
         o.apply_bc(Q)
         R, J, Xi = o.inner(o.residual(Q)), o.inner(o.J), o.inner(X)
         sel = (slice(0, -1), slice(2, -3), slice(3, -3))

@@ -18,6 +18,8 @@ import pytest
 
 from paper_2003_09926_gb300 import workloads as W
 
+import states as ST
+
 NG = 2
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden")
@@ -43,7 +45,7 @@ def _set_all(o, Qin):
 
 def _uniform(shape, rho, u, v, w, p):
     one = np.ones(shape)
-    return W.primitive_to_conserved(rho * one, u * one, v * one, w * one, p * one)
+    return ST.primitive_to_conserved(rho * one, u * one, v * one, w * one, p * one)
 
 
 # ---------------------------------------------------------------------------
@@ -150,14 +152,14 @@ def test_discrete_conservation_periodic(orc):
     all active on a noisy field."""
     d = W.periodic_grid(12, 10, 8, hi=(2.0, 1.5, 1.2), map_amp=0.3, map_seed=5)
     o = orc.Oracle(d, W.jet_flow(re=2e3, cs=0.18))
-    Q = _set_all(o, W.random_state((8, 10, 12), seed=7))
+    Q = _set_all(o, ST.random_state((8, 10, 12), seed=7))
     s0 = o.diagnostics(Q)["sum"]
     o.run(Q, 20, cfl=0.5)
     s1 = o.diagnostics(Q)["sum"]
     scale = np.array([abs(s0[0]), abs(s0[1]) + abs(s0[0]), abs(s0[2]) + abs(s0[0]), abs(s0[3]) + abs(s0[0]),
                       abs(s0[4])])
     assert (np.abs(s1 - s0) / scale).max() <= 1e-13
-    assert np.abs(o.inner(Q) - o.inner(_set_all(o, W.random_state((8, 10, 12), seed=7)))).max() > 1e-4
+    assert np.abs(o.inner(Q) - o.inner(_set_all(o, ST.random_state((8, 10, 12), seed=7)))).max() > 1e-4
 
 
 @pytest.mark.parametrize("k4", [0.0, 1.0 / 256.0, 1.0 / 32.0])
@@ -179,7 +181,7 @@ def test_rk_amplification_factor(orc, k4, mode):
     th = 2 * np.pi * mode / N
     rho = (1 + eps * np.cos(th * np.arange(N))).reshape(1, 1, N)
     one = np.ones((1, 1, N))
-    Q = _set_all(o, W.primitive_to_conserved(rho, U * one, 0 * one, 0 * one, one / 1.4))
+    Q = _set_all(o, ST.primitive_to_conserved(rho, U * one, 0 * one, 0 * one, one / 1.4))
     dt = 0.8 * h / (U + 1)
     r0 = np.fft.fft(o.inner(Q)[0, 0, 0] - 1)[mode]
     o.step(Q, dt=dt)
@@ -217,7 +219,7 @@ def test_isentropic_vortex_second_order(orc, mapped):
         d = W.periodic_grid(N, N, 1, lo=(-6, -6, 0), hi=(6, 6, h), map_amp=0.1 if mapped else 0.0, map_seed=2)
         o = orc.Oracle(d, W.jet_flow(re=0.0, cs=0.0, ic=W.IC_QUIESCENT))
         X = o.inner(o.X)
-        Q = _set_all(o, W.primitive_to_conserved(*_vortex(X[0], X[1], 0.0, L, 0.5, 0.3)))
+        Q = _set_all(o, ST.primitive_to_conserved(*_vortex(X[0], X[1], 0.0, L, 0.5, 0.3)))
         n = int(np.ceil(T / (0.4 * h / 1.8)))
         o.run(Q, n, dt=T / n)
         rho_e = _vortex(X[0], X[1], T, L, 0.5, 0.3)[0]
@@ -244,7 +246,7 @@ def test_sod_shock_tube_converges(orc):
         inside = (x >= 0.25) & (x < 0.75)
         rho = np.where(inside, 1.0, 0.125).reshape(1, 1, N)
         p = np.where(inside, 1.0, 0.1).reshape(1, 1, N)
-        Q = _set_all(o, W.primitive_to_conserved(rho, 0 * rho, 0 * rho, 0 * rho, p))
+        Q = _set_all(o, ST.primitive_to_conserved(rho, 0 * rho, 0 * rho, 0 * rho, p))
         n = int(np.ceil(T / (0.3 * h / 2.2)))
         o.run(Q, n, dt=T / n)
         xi = np.where(x < 0.5, (0.25 - x) / T, (x - 0.75) / T)
@@ -263,7 +265,7 @@ def test_axis_permutation_equivariance(orc):
     d = W.periodic_grid(n, n, n, map_amp=0.25, map_seed=3)
     f = W.jet_flow(re=500.0, cs=0.18)
     o1 = orc.Oracle(d, f)
-    Qin = W.random_state((n, n, n), seed=11)
+    Qin = ST.random_state((n, n, n), seed=11)
     Q1 = _set_all(o1, Qin)
     R1 = o1.residual(Q1)
     # new axis a' = old axis a+1:  new x-coord = old y-coord, array axes rolled
@@ -289,7 +291,7 @@ def _fill_padded(o, fn):
     """Evaluate a primitive-field function at every padded node (no BCs)."""
     X = o.X
     rho, u, v, w, p = fn(X[0], X[1], X[2])
-    return np.ascontiguousarray(W.primitive_to_conserved(rho, u, v, w, p))
+    return np.ascontiguousarray(ST.primitive_to_conserved(rho, u, v, w, p))
 
 
 def _viscous_part(orc, d, f, fn):
@@ -532,7 +534,7 @@ def test_riemann_farfield_invariants(orc):
         ut = rng.normal(size=3)
         ut -= (ut @ n) * n
         u = ut + un * n
-        qi = W.primitive_to_conserved(rho, *u, p)
+        qi = ST.primitive_to_conserved(rho, *u, p)
         qb = o.riemann(qi, n)
         rb, ub, pb = _prim(qb)
         cb = math.sqrt(g * pb / rb)
@@ -545,11 +547,11 @@ def test_riemann_farfield_invariants(orc):
             assert pb / rb ** g == pytest.approx(1.0 / g, rel=1e-12)
             np.testing.assert_allclose(ub - (ub @ n) * n, 0.0, atol=1e-13)
     n = np.array([1.0, 0, 0])
-    q_out = W.primitive_to_conserved(1.0, 1.5, 0.2, 0.0, 1 / g)
+    q_out = ST.primitive_to_conserved(1.0, 1.5, 0.2, 0.0, 1 / g)
     np.testing.assert_array_equal(o.riemann(q_out, n), q_out)
-    q_in = W.primitive_to_conserved(1.0, -1.5, 0.2, 0.0, 1 / g)
-    np.testing.assert_allclose(o.riemann(q_in, n), W.primitive_to_conserved(1.0, 0, 0, 0, 1 / g), rtol=1e-15)
-    fs = W.primitive_to_conserved(1.0, 0, 0, 0, 1 / g)
+    q_in = ST.primitive_to_conserved(1.0, -1.5, 0.2, 0.0, 1 / g)
+    np.testing.assert_allclose(o.riemann(q_in, n), ST.primitive_to_conserved(1.0, 0, 0, 0, 1 / g), rtol=1e-15)
+    fs = ST.primitive_to_conserved(1.0, 0, 0, 0, 1 / g)
     np.testing.assert_allclose(o.riemann(fs, n), fs, rtol=1e-14, atol=1e-15)
 
 
@@ -602,7 +604,7 @@ def test_jet_initial_state_and_inflow(orc):
 
 def test_periodic_ghosts_wrap(orc):
     o = orc.Oracle(W.periodic_grid(5, 4, 3), W.jet_flow())
-    Q = _set_all(o, W.random_state((3, 4, 5), seed=2))
+    Q = _set_all(o, ST.random_state((3, 4, 5), seed=2))
     np.testing.assert_array_equal(Q[..., 0], Q[..., 5])
     np.testing.assert_array_equal(Q[..., 1], Q[..., 6])
     np.testing.assert_array_equal(Q[..., 7], Q[..., 2])
@@ -632,3 +634,175 @@ def test_jet_case_runs_and_stays_physical(orc):
     dg = o.diagnostics(Q)
     assert dg["nonfinite"] == 0 and dg["rho_min"] > 0.8 and dg["p_min"] > 0.5 / 1.4
     assert dg["mach_max"] < 1.6
+
+
+# ---------------------------------------------------------------------------
+# readings R5 (mapping), R7 (jet profile and noise) and R8 (edge tie-break),
+# each evaluated by hand from its stated definition
+# ---------------------------------------------------------------------------
+
+_M64 = 0xFFFFFFFFFFFFFFFF
+
+
+def _splitmix64(x: int) -> int:
+    """SplitMix64 output for state x, written from the generator's published
+    definition (the same vectors as tests/golden/splitmix64.txt pin it)."""
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def test_python_splitmix64_matches_published_vectors():
+    gamma = 0x9E3779B97F4A7C15
+    for seed, idx, out in _golden("splitmix64.txt"):
+        assert _splitmix64((int(seed) + int(idx) * gamma) & _M64) == int(out)
+
+
+def _unit53(r: int) -> float:
+    return (r >> 11) / 9007199254740992.0
+
+
+def test_jet_profile_hand_values(orc):
+    """R7: u(r) = (M/2) (1 - tanh((r - 0.5) / (2 * 0.05))) with M = 1.4.  At
+    r = 0.5 exactly M/2; one momentum thickness pair out (r = 0.6, 0.4)
+    M/2 (1 -+ tanh 1).  A width of theta instead of 2 theta, a wrong radius
+    or a wrong sign fails."""
+    f = orc.make_flow(W.jet_flow())
+    prof = lambda r: float(orc.lib().orc_jet_profile(f, r))  # noqa: E731
+    M = 1.4
+    assert prof(0.5) == 0.5 * M
+    assert prof(0.6) == pytest.approx(0.5 * M * (1.0 - math.tanh(1.0)), rel=1e-14)
+    assert prof(0.4) == pytest.approx(0.5 * M * (1.0 + math.tanh(1.0)), rel=1e-14)
+    assert prof(0.0) == pytest.approx(0.5 * M * (1.0 + math.tanh(5.0)), rel=1e-15)
+    assert prof(1.5) == pytest.approx(0.5 * M * (1.0 - math.tanh(10.0)), rel=1e-12)
+
+
+def test_inflow_plane_is_the_hand_profile(orc):
+    """The x = 0 plane of the config-0 jet holds rho = 1, p = 1/gamma,
+    v = w = 0 and u = the R7 profile at r = sqrt(y^2 + z^2), with y and z
+    from the R4 stretching formula evaluated here:
+    y(s) = H G(s) / G(1), G(s) = s - (c/H)[tanh((H s - r_c)/w) + tanh((H s + r_c)/w)]."""
+    c = W.config0()
+    gd = c["grid"]
+    o = orc.Oracle(gd, c["flow"])
+    q = o.inner(o.init(c["seed"]))
+    H, cc, w, rc = 8.0, gd["stretch_c"], gd["stretch_w"], gd["cluster_r"]
+
+    def G(s):
+        return s - (cc / H) * (math.tanh((H * s - rc) / w) + math.tanh((H * s + rc) / w))
+
+    def coord(idx, n):
+        return H * G(-1.0 + 2.0 * idx / (n - 1)) / G(1.0)
+
+    M = c["flow"]["mach"]
+    for k, j in ((0, 0), (5, 9), (16, 15), (31, 20), (13, 17)):
+        y, z = coord(j, gd["nj"]), coord(k, gd["nk"])
+        u = 0.5 * M * (1.0 - math.tanh((math.hypot(y, z) - 0.5) / 0.1))
+        assert q[0, k, j, 0] == 1.0
+        assert q[1, k, j, 0] == pytest.approx(u, rel=1e-13, abs=1e-15)
+        assert q[2, k, j, 0] == 0.0 and q[3, k, j, 0] == 0.0
+        assert q[4, k, j, 0] == pytest.approx(1.0 / (1.4 * 0.4) + 0.5 * u * u, rel=1e-14)
+
+
+def test_initial_noise_hand_values(orc):
+    """R7 noise: u_m += noise * M * (2 xi - 1), xi = top 53 bits of
+    SplitMix64(seed XOR (3 lin + m)) / 2^53, lin = i + ni (j + nj k).  The
+    transverse momenta of an interior node (rho = 1) are exactly that
+    value; the axial one adds it to the profile.  A wrong linear index, a
+    wrong stride 3 or a seed not XORed in fails."""
+    gd = W.jet_grid(14, 10, 9)
+    fl = W.jet_flow()
+    o = orc.Oracle(gd, fl)
+    seed = 0x5DEECE66D
+    q = o.inner(o.init(seed))
+    amp = fl["noise"] * fl["mach"]
+    ni, nj = gd["ni"], gd["nj"]
+    X = o.inner(o.X)
+    for (i, j, k) in ((5, 7, 3), (1, 1, 1), (12, 8, 7), (7, 2, 5)):
+        lin = i + ni * (j + nj * k)
+        xi = [_unit53(_splitmix64(seed ^ (3 * lin + m))) for m in range(3)]
+        r = math.hypot(X[1, k, j, i], X[2, k, j, i])
+        prof = 0.5 * fl["mach"] * (1.0 - math.tanh((r - 0.5) / 0.1))
+        assert q[0, k, j, i] == 1.0
+        assert q[2, k, j, i] == amp * (2.0 * xi[1] - 1.0)
+        assert q[3, k, j, i] == amp * (2.0 * xi[2] - 1.0)
+        assert q[1, k, j, i] == pytest.approx(prof + amp * (2.0 * xi[0] - 1.0), rel=1e-15, abs=1e-16)
+
+
+def test_mapping_offsets_hand_values(orc):
+    """R5: x_d = base_d + a h_d prod_e sin(2 pi m_de idx_e / P_e + theta_de),
+    m_de = 1 + SplitMix64(seed XOR 2c) mod 3 and theta_de = 2 pi * top-53
+    bits of SplitMix64(seed XOR (2c + 1)), c = 3d + e; P_e = N_e - 1 (N_e in
+    a periodic direction).  On an unstretched box the base coordinate and
+    the spacing h_d are uniform, so every offset is evaluated here at
+    interior, boundary and ghost indices.  A wrong wave-number draw, a
+    wrong phase, N instead of N - 1 or a swapped (d, e) fails."""
+    seed = 987654321
+    gd = W.jet_grid(11, 9, 7, map_amp=0.05, map_seed=seed)
+    gd["stretch_c"] = 0.0
+    gd["bc"][4] = gd["bc"][5] = W.BC_PERIODIC  # z periodic: P = N
+    o = orc.Oracle(gd, W.jet_flow())
+    n = (gd["ni"], gd["nj"], gd["nk"])
+    lo, hi = gd["lo"], gd["hi"]
+    per = (False, False, True)
+    P = [n[e] if per[e] else n[e] - 1 for e in range(3)]
+    h = [(hi[d] - lo[d]) / P[d] for d in range(3)]
+    m = [[1 + _splitmix64(seed ^ (2 * (3 * d + e))) % 3 for e in range(3)] for d in range(3)]
+    th = [[2.0 * math.pi * _unit53(_splitmix64(seed ^ (2 * (3 * d + e) + 1))) for e in range(3)] for d in range(3)]
+    mo, tho = o.map_params()
+    np.testing.assert_array_equal(mo, np.array(m))
+    np.testing.assert_array_equal(tho, np.array(th))
+    for idx in ((3, 4, 2), (0, 0, 0), (10, 8, 6), (-2, 5, -1), (12, -1, 8), (7, 2, 4)):
+        for d in range(3):
+            base = lo[d] + h[d] * idx[d]
+            prod = 1.0
+            for e in range(3):
+                prod *= math.sin(2.0 * math.pi * m[d][e] * idx[e] / P[e] + th[d][e])
+            want = base + 0.05 * h[d] * prod
+            got = o.X[d, idx[2] + NG, idx[1] + NG, idx[0] + NG]
+            assert got == pytest.approx(want, rel=1e-13, abs=1e-13), (idx, d)
+
+
+def test_boundary_edge_and_corner_tie_break(orc):
+    """R8: on edges and corners the face latest in the order y-, y+, z-, z+,
+    x+, x- sets the node.  A uniform state u = (2, 0.3, -2) (c = 1) makes
+    every face's value distinct: x- is the inflow profile, x+ and z- see
+    supersonic outflow (a copy of the adjacent interior node), z+ supersonic
+    inflow (air at rest), y- and y+ subsonic Riemann states."""
+    gd = W.jet_grid(8, 7, 6)
+    gd["stretch_c"] = 0.0
+    o = orc.Oracle(gd, W.jet_flow())
+    ni, nj, nk = gd["ni"], gd["nj"], gd["nk"]
+    g = 1.4
+    Q = _set_all(o, _uniform((nk, nj, ni), 1.0, 2.0, 0.3, -2.0, 1.0 / g))
+    q = o.inner(Q)
+    rest = ST.primitive_to_conserved(1.0, 0.0, 0.0, 0.0, 1.0 / g)
+    X = o.inner(o.X)
+
+    def inflow(i, j, k):
+        r = math.hypot(X[1, k, j, i], X[2, k, j, i])
+        return ST.primitive_to_conserved(1.0, 0.5 * 1.4 * (1 - math.tanh((r - 0.5) / 0.1)), 0.0, 0.0, 1.0 / g)
+
+    def interior(i, j, k):
+        cl = lambda a, n: min(max(a, 1), n - 2)  # noqa: E731
+        return q[:, cl(k, nk), cl(j, nj), cl(i, ni)]
+
+    # the faces' own values, away from edges
+    yface = q[:, 3, 0, 4]
+    assert abs(yface[0] - 1.0) > 1e-3 and abs(q[0, 3, nj - 1, 4] - 1.0) > 1e-3
+    np.testing.assert_array_equal(q[:, 0, 3, 4], interior(4, 3, 0))   # z-: copy
+    np.testing.assert_allclose(q[:, nk - 1, 3, 4], rest, rtol=1e-15)   # z+: at rest
+    cases = [  # (i, j, k) -> expected winner
+        ((0, 0, 3), "x-"), ((0, nj - 1, 0), "x-"), ((0, 2, nk - 1), "x-"),
+        ((ni - 1, 0, 3), "x+"), ((ni - 1, nj - 1, nk - 1), "x+"), ((ni - 1, 3, 0), "x+"),
+        ((4, 0, 0), "z-"), ((4, nj - 1, 0), "z-"), ((4, 0, nk - 1), "z+"), ((4, nj - 1, nk - 1), "z+"),
+    ]
+    for (i, j, k), face in cases:
+        got = q[:, k, j, i]
+        if face == "x-":
+            np.testing.assert_allclose(got, inflow(i, j, k), rtol=1e-14, atol=1e-15)
+        elif face in ("x+", "z-"):
+            np.testing.assert_array_equal(got, interior(i, j, k))
+        else:
+            np.testing.assert_allclose(got, rest, rtol=1e-15)
