@@ -231,6 +231,113 @@ def profile_steps(jz, torch, g, steps: int, cfl: float):
     return prof
 
 
+def host_cpu() -> dict:
+    """nproc and the CPU model of this host (from /proc/cpuinfo, else lscpu)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.split(":")[0].strip() in ("Model name", "Vendor ID"):
+                    model = line.split(":", 1)[1].strip()
+                    if line.startswith("Model name"):
+                        break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+# Riemann far-field branch of a boundary value (the boundary-condition
+# reading R8): 0 supersonic inflow (u_n <= -c), 1 subsonic with the outside
+# entropy, 2 subsonic with the inside entropy, 3 supersonic outflow
+# (u_n >= c); the subsonic split is the sign of the characteristic average
+# u_n + 2 (c - c_inf) / (gamma - 1) against air at rest (c_inf = 1).
+def riemann_branch(q, n, gamma=1.4):
+    rho = q[0]
+    u = q[1:4] / rho
+    p = (gamma - 1.0) * (q[4] - 0.5 * rho * (u * u).sum(axis=0))
+    c = np.sqrt(gamma * p / rho)
+    un = (u * n).sum(axis=0)
+    sub_out = un + 2.0 * (c - 1.0) / (gamma - 1.0) > 0.0
+    return np.where(un >= c, 3, np.where(un <= -c, 0, np.where(sub_out, 2, 1)))
+
+
+def error_classes(Q, Qref, S, bc, gamma=1.4):
+    """FP32-vs-FP64 error of every node, by class: inflow-face nodes;
+    far-field face nodes whose Riemann branch (riemann_branch, from the
+    adjacent interior node and the outward unit normal S^k/|S^k| of the face
+    that sets the node: later faces in the order y-, y+, z-, z+, x+, x- win)
+    is the same in both states, and those where it differs; nodes at distance
+    1, 2 and >= 3 from the nearest non-periodic face.  Q, Qref: [5][nk][nj][ni];
+    S: [>= 9][nk][nj][ni] metrics; bc: the six face kinds (0 periodic, 1
+    inflow, 2 far field).  Error of a class: max over variables of
+    max|Q - Qref| over its nodes / max|Qref| over all nodes."""
+    nk, nj, ni = Q.shape[1:]
+    n = (ni, nj, nk)
+    big = 1 << 30
+    idx = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")  # k, j, i
+    dist = np.full((nk, nj, ni), big)
+    for d in range(3):
+        if bc[2 * d] != 0:
+            a = idx[2 - d]
+            dist = np.minimum(dist, np.minimum(a, n[d] - 1 - a))
+    face = np.full((nk, nj, ni), -1)
+    for f in (2, 3, 4, 5, 1, 0):
+        d = f // 2
+        if bc[f] == 0:
+            continue
+        a = idx[2 - d]
+        face[a == (0 if f % 2 == 0 else n[d] - 1)] = f
+    scale = np.abs(Qref).reshape(5, -1).max(axis=1)
+    scale = np.where(scale > 0, scale, 1.0)  # an all-zero variable: absolute error
+    diff = np.abs(Q - Qref)
+
+    def stat(mask):
+        cnt = int(mask.sum())
+        if cnt == 0:
+            return {"nodes": 0, "max_rel": 0.0, "max_rel_per_variable": [0.0] * 5}
+        per = [float(diff[v][mask].max() / scale[v]) for v in range(5)]
+        return {"nodes": cnt, "max_rel": max(per), "max_rel_per_variable": per}
+
+    out = {}
+    inflow = np.isin(face, [f for f in range(6) if bc[f] == 1])
+    out["inflow_face"] = stat(inflow)
+    ff = np.zeros_like(inflow)
+    differs = np.zeros_like(inflow)
+    for f in range(6):
+        if bc[f] != 2:
+            continue
+        m = face == f
+        if not m.any():
+            continue
+        kk, jj, ii = np.nonzero(m)
+        ci = [np.clip(ii, 1, ni - 2), np.clip(jj, 1, nj - 2), np.clip(kk, 1, nk - 2)]
+        d = f // 2
+        sg = -1.0 if f % 2 == 0 else 1.0
+        nv = np.stack([S[3 * d + e][kk, jj, ii] for e in range(3)])
+        nv = sg * nv / np.sqrt((nv * nv).sum(axis=0))
+        b32 = riemann_branch(Q[:, ci[2], ci[1], ci[0]], nv, gamma)
+        b64 = riemann_branch(Qref[:, ci[2], ci[1], ci[0]], nv, gamma)
+        ff[kk, jj, ii] = True
+        differs[kk, jj, ii] = b32 != b64
+    out["farfield_face_same_branch"] = stat(ff & ~differs)
+    out["farfield_face_branch_differs"] = stat(ff & differs)
+    out["interior_d1"] = stat(dist == 1)
+    out["interior_d2"] = stat(dist == 2)
+    out["interior_d3plus"] = stat(dist >= 3)
+    out["all_nodes"] = stat(np.ones_like(inflow))
+    return out
+
+
 def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
     """The oracle as it stands on the host cores: one RK step of the same jet
     workload, timed (metric generation excluded)."""
@@ -254,7 +361,7 @@ def cpu_oracle_baseline(cfg: dict, sample_shape=(256, 192, 192)):
     o1.run(Q1, 3, cfl=c0["cfl"])
     sec1 = time.perf_counter() - t1
     oracle.set_threads(cores)
-    return {"value": pts * 5 / sec / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": pts * 5 / sec / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle", **host_cpu(),
             "sample": f"one RK step (5 stages) of the {sample_shape[0]}x{sample_shape[1]}x{sample_shape[2]} mapped jet "
                       f"grid in FP64, OpenMP over k-planes, {sec:.1f} s",
             "single_thread": {"value": interior_points(c0["grid"]) * 5 * 3 / sec1 / 1e6, "unit": UNIT, "cores": 1,
@@ -380,31 +487,56 @@ def bench_billion(jz, torch, W, local: int, steps: int, cfl: float = 0.5):
     return out
 
 
-def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 32, base64_n: int = 6,
-                  pts_hi: float = 2e6):
-    """Continuous batching on a bounded serving trace: log-uniform 1e5..pts_hi
-    points per case (2e6 by default; the full 2e7 range with --serving-full),
-    50..500 steps, Poisson arrivals at 70% of the measured batched capacity,
-    150 GB HBM budget, 10-step slices; against the same trace one case at a
-    time (FP32 unbatched, and FP64 on its first cases)."""
+def fifo_extrapolation(trace, rate_mpt: float) -> dict:
+    """Latencies of serving `trace` one case at a time in arrival order at a
+    fixed rate (Mpt-stage/s): start = max(arrival, previous finish),
+    finish = start + case work / rate."""
+    from paper_2003_09926_gb300 import serve
+    t, lat, work = 0.0, [], 0.0
+    for r in sorted(trace, key=lambda r: (r.arrival, r.rid)):
+        w = serve.updated_points(r.grid) * 5 * r.steps
+        t = max(t, r.arrival) + w / (rate_mpt * 1e6)
+        lat.append(t - r.arrival)
+        work += w
+    span = t - min(r.arrival for r in trace)
+    return {"completed": len(lat), "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(np.mean(lat)),
+            "makespan_s": span, "throughput_mpt_stage_s": work / span / 1e6}
+
+
+def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 256, base64_n: int = 4,
+                  pts_hi: float = 2e7, orders=("remaining",), fill: int = 4 * 10**6):
+    """Continuous batching on the serving trace: log-uniform 1e5..pts_hi
+    points per case (the configuration's 2e7 by default), 50..500 steps,
+    Poisson arrivals at 70% of the measured batched capacity, 150 GB HBM
+    budget, 10-step slices; against the same trace served one case at a
+    time in FP32, and in plain FP64 on its first cases with the full trace
+    extrapolated at the FP64 rate measured there."""
     from paper_2003_09926_gb300 import serve
     cfg = W.config4(nreq=nreq, pts_hi=pts_hi)
     work = np.mean([interior_points(r["grid"]) * 5 * r["steps"] for r in cfg["requests"]])
     rate = 0.7 * capacity * 1e6 / work
     trace = serve.poisson_trace(cfg, rate)
-    fill = 4 * 10**6
-    srv = serve.Server(150 * 10**9, slice_steps=10, device=local, fill_points=fill)
-    res = srv.run(trace)
     out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..{pts_hi:.0e} points, 50..500 steps, seed 4",
-           "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10,
-           "fp32_continuous_batching": dict(serve.summarize(res), fill_points=fill,
-                                            policy="oldest cases first until they hold fill_points points"),
-           "peak_resident_bytes": srv.peak_bytes, "slices": srv.slices}
-    srv_all = serve.Server(150 * 10**9, slice_steps=10, device=local)
-    out["fp32_batching_all_resident"] = serve.summarize(srv_all.run(trace))
+           "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10}
+    for order in orders:
+        srv = serve.Server(150 * 10**9, slice_steps=10, device=local, fill_points=fill, order=order)
+        res = srv.run(trace)
+        key = "fp32_continuous_batching" if order == orders[0] else f"fp32_continuous_batching_{order}"
+        out[key] = dict(serve.summarize(res), fill_points=fill, order=order,
+                        policy=("least remaining work first" if order == "remaining" else "oldest first")
+                        + " until the selected cases hold fill_points points; a single case runs alone",
+                        peak_resident_bytes=srv.peak_bytes, slices=srv.slices)
     out["fp32_one_at_a_time"] = serve.summarize(serve.serve_one_at_a_time(trace, W.P32, device=local))
-    out["fp64_one_at_a_time_first_cases"] = dict(
-        serve.summarize(serve.serve_one_at_a_time(trace[:base64_n], W.P64, device=local)), cases=base64_n)
+    first = serve.serve_one_at_a_time(trace[:base64_n], W.P64, device=local)
+    busy = sum(r.finished - r.admitted for r in first)
+    w64 = sum(r.points * 5 * r.steps for r in first)
+    rate64 = w64 / busy / 1e6
+    out["fp64_one_at_a_time_first_cases"] = dict(serve.summarize(first), cases=base64_n)
+    out["fp64_one_at_a_time_extrapolated"] = dict(
+        fifo_extrapolation(trace, rate64), fp64_rate_mpt_stage_s=rate64,
+        note=f"extrapolated, not measured: every case of the trace served in arrival order at the FP64 rate "
+             f"measured on the first {base64_n} cases ({rate64:.0f} Mpt-stage/s)")
     return out
 
 
@@ -434,7 +566,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "c1_jet_256x192x192 (per step: 64x48x48 sample of the same jet and mapping)",
                        "precision": "FP64 oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", **host_cpu(),
                              "sample": f"{args.steps} RK steps of a 64x48x48 sample of the mapped jet workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -457,8 +589,11 @@ def main(argv=None):
                     help="skip the paper's thirteen scalability meshes as cylinders (3.7e5 .. 1e9 points, about 10 s)")
     ap.add_argument("--err-steps", type=int, default=200,
                     help="steps of the FP32-vs-FP64 error runs (the 256x192x192 configuration's 200)")
-    ap.add_argument("--serving-full", action="store_true",
-                    help="serve the full 1e5..2e7-point trace (about a minute) instead of the bounded one")
+    ap.add_argument("--serving-quick", action="store_true",
+                    help="serve a bounded 32-case trace of at most 2e6 points instead of the configuration's 256 "
+                         "cases of 1e5..2e7 points (several minutes)")
+    ap.add_argument("--serving-orders", default="remaining",
+                    help="comma-separated slice orders to serve the trace with (remaining, arrival)")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -510,6 +645,7 @@ def main(argv=None):
     ref = jz.Grid(dict(grid, precision=W.P64), device=local).init(cfg["flow"], cfg["seed"])
     ref.nsteps(err_steps, cfl=cfg["cfl"])
     Qref = ref.download()
+    Sref = ref.metrics()
     ref.close()
     del ref
     errors = {}
@@ -524,9 +660,10 @@ def main(argv=None):
             "max_rel_interior": max(per_var),
             "max_rel_interior_per_variable": per_var,
             "max_rel_all_nodes": max(float(np.abs(Q[v] - Qref[v]).max() / np.abs(Qref[v]).max()) for v in range(5)),
-            "l2_rel": max(float(np.sqrt(np.mean((Q[v] - Qref[v]) ** 2) / np.mean(Qref[v] ** 2))) for v in range(5))}
+            "l2_rel": max(float(np.sqrt(np.mean((Q[v] - Qref[v]) ** 2) / np.mean(Qref[v] ** 2))) for v in range(5)),
+            "classes": error_classes(Q, Qref, Sref, grid["bc"])}
         del g
-    del Qref
+    del Qref, Sref
 
     # end to end through the public C ABI with host buffers: the initial state
     # uploaded from pinned host memory, every step's diagnostics (the step's
@@ -614,14 +751,16 @@ def main(argv=None):
             "e2e": e2e,
             "variants": {W.PRECISION_NAMES[p]: r for p, r in results.items()},
             "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
-                                   "interior": "nodes at least 3 from every face; far-field face nodes can differ by O(1) where the Riemann condition switches branch (sign of u_n, |u_n| = c) between precisions"},
+                                   "interior": "nodes at least 3 from every face",
+                                   "classes": "every node by class: inflow face; far-field face nodes whose Riemann branch (supersonic in / subsonic outside entropy / subsonic inside entropy / supersonic out, from the adjacent interior node) is the same in both precisions, and those where it differs; nodes at distance 1, 2 and >= 3 from the nearest face"},
             "fp64_vs_fp32_speedup": results[head]["value"] / results[W.P64]["value"]}
     if not args.no_batched:
         line["batched"] = bench_batched(jz, torch, W, local, steps=max(10, args.steps // 5), steps64=2)
     if not args.no_serving:
         cap = line["batched"]["fp32_batched"]["value"] if "batched" in line else results[head]["value"]
-        line["serving"] = (bench_serving(jz, torch, W, local, cap, pts_hi=2e7, base64_n=2) if args.serving_full
-                           else bench_serving(jz, torch, W, local, cap))
+        orders = tuple(args.serving_orders.split(","))
+        line["serving"] = (bench_serving(jz, torch, W, local, cap, nreq=32, pts_hi=2e6, orders=orders)
+                           if args.serving_quick else bench_serving(jz, torch, W, local, cap, orders=orders))
     if not args.no_cylinder:
         line["cylinder"] = bench_cylinder(jz, torch, W, local, steps=max(10, args.steps // 4), steps64=2)
     if not args.no_billion and world == 1:

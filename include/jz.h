@@ -233,6 +233,15 @@ int jz_diagnostics_async(jz_grid* g, jz_diag* out);
  * nodes from the FP32 one).  Synchronises the stream. */
 int jz_state_download(jz_grid* g, double* host, size_t n);
 
+/* Copy the metric terms the kernels use to host memory (Section 3: the
+ * generalised curvilinear transformation): n = 10*ni*nj*nk doubles, layout
+ * [f][k][j][i], f = 3k+m for S^k_m = (d xi_k / d x_m)/J and f = 9 for J,
+ * ghosts excluded, widened from the grid's metric type (FP32 for JZ_P32 and
+ * JZ_P32_S64).  Uses the grid's stage buffer as staging, so call it between
+ * steps; synchronises the stream.  JZ_EINVAL for a wrong n or a null
+ * pointer. */
+int jz_metrics_download(jz_grid* g, double* host, size_t n);
+
 /* Replace the state from host memory (layout as jz_state_download; values
  * at boundary nodes are overwritten by the boundary conditions, which are
  * applied after the upload; a JZ_P32_S64 grid keeps the FP64 values of its
@@ -352,6 +361,19 @@ int jz_set_tiling(jz_grid* g, int kc);
  * for other variants.  A batch uses its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
+/* Test of the bounded waits (SURVEY failure detection; the paper has no
+ * counterpart).  on = 1: every TMA copy that the grid's stage kernels issue
+ * expects 16 bytes more than it delivers, so no staging wait can complete,
+ * and the waits give up after 2^16 SM cycles instead of about a second.
+ * Each stage kernel then takes its timeout path: it records the failure in
+ * the grid's sticky error flag, completes the missing bytes itself, waits
+ * for its real copies to land and returns; nothing traps or hangs, and
+ * jz_diagnostics reports JZ_ETIMEOUT.  The state is invalid afterwards:
+ * set on = 0 and call jz_state_init (or jz_state_upload after it) to clear
+ * the flag and continue.  Affects single-grid launches only (jz_rk_step,
+ * jz_nsteps); batches ignore it.  JZ_EINVAL for other values of on. */
+int jz_set_stall_test(jz_grid* g, int on);
+
 /* Tile shape (ti x tj nodes in i and j) of the FP32 vector-record stage
  * kernel of this grid: 32 x 16 (default), 16 x 32 or 16 x 16, each a build of
  * the same kernel (one CTA per SM; 16 x 32 wastes less of a tile on grids
@@ -384,11 +406,13 @@ int jz_set_tile_shape(jz_grid* g, int ti, int tj);
  * stream: cudaStream_t as void* (NULL = legacy default stream).
  * n_nodes must not exceed 268,435,456 (2^28; JZ_EINVAL beyond).  The work is
  * enqueued asynchronously; results are summed in a fixed order (bitwise
- * reproducible).  The first call on a device looks up the static array's
- * device address with that device current and must come before any other
- * use of the array on that device.  Every call shares the one array, which
- * keeps the last call's contents; calls whose kernels may overlap on the GPU
- * (unordered streams) race on it and must not be issued. */
+ * reproducible).  Every call looks up the static array's device address for
+ * the device current at the call (a lookup, no allocation); the first call on
+ * a device also loads the library's device code there, so make it before any
+ * stream capture.  Every call shares the one array, which keeps the last
+ * call's contents (the call clears the counter it needs zeroed); calls whose
+ * kernels may overlap on the GPU (unordered streams) race on it and must not
+ * be issued. */
 int jz_state_diagnostics_static(long long n_nodes, int fp64, const void* Q, const double* vol, double gamma,
                                 double* out, void* stream);
 

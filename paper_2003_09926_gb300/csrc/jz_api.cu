@@ -169,6 +169,20 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
 
 struct EventPair { cudaEvent_t a, b; int cls; };
 
+int device_sm_count() {
+  static std::atomic<int> cache[64];  // 0: not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
 }  // namespace jz
 
 using namespace jz;
@@ -273,7 +287,7 @@ int check_dt(double cfl, double dt_fixed) {
 int default_kc(const Layout& L, StageTiling t, int prec) {
   long long tiles = (long long)((L.hi[0] + t.ti) / t.ti) * ((L.hi[1] + t.tj) / t.tj);
   int nz = L.hi[2] - L.lo[2] + 1;
-  long long slots = 152LL * stage_ctas_per_sm(prec);
+  long long slots = (long long)device_sm_count() * stage_ctas_per_sm(prec);
   int best = nz;
   double best_cost = 1e300;
   for (int kc = 1; kc <= nz; ++kc) {
@@ -642,6 +656,20 @@ int jz_state_download(jz_grid* g, double* host, size_t n) {
   return JZ_OK;
 }
 
+int jz_metrics_download(jz_grid* g, double* host, size_t n) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!host) return fail(JZ_EINVAL, "null host buffer");
+  const size_t N = state_count(g) / 5;
+  if (n != 10 * N) return fail(JZ_EINVAL, "host buffer holds %zu values, metrics have %zu", n, 10 * N);
+  double* staging = (double*)g->dev.QA;  // one FP64 field fits the free stage buffer QA
+  for (int f = 0; f < 10; ++f) {
+    JZ_CUDA(launch_pack_metric(g->dev, f, staging, g->stream));
+    JZ_CUDA(cudaMemcpyAsync(host + (size_t)f * N, staging, N * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  }
+  JZ_CUDA(cudaStreamSynchronize(g->stream));
+  return JZ_OK;
+}
+
 int jz_state_upload(jz_grid* g, const double* host, size_t n) {
   if (int rc = check_grid(g, true)) return rc;
   if (!host) return fail(JZ_EINVAL, "null host buffer");
@@ -706,6 +734,14 @@ int jz_set_stage_variant(jz_grid* g, int variant) {
   g->dev.variant = variant;
   drop_graph(g);
   return build_maps(g->dev);  // the two kernels may stage different tiles
+}
+
+int jz_set_stall_test(jz_grid* g, int on) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (on != 0 && on != 1) return fail(JZ_EINVAL, "stall test flag must be 0 or 1");
+  g->dev.stall_test = on;
+  drop_graph(g);  // captured launches carry the flag
+  return JZ_OK;
 }
 
 int jz_set_tile_shape(jz_grid* g, int ti, int tj) {

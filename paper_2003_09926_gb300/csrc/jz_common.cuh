@@ -122,7 +122,7 @@ struct Scalars {
   jz_diag out;        // the same in the public layout (copied out by jz_diagnostics_async)
 };
 
-constexpr int RED_BLOCKS = 1216;  // fixed grid of the reductions (8 x 152 SMs)
+constexpr int RED_BLOCKS = 1216;  // capacity of the reduction partials (grids are clamped to it)
 constexpr int RED_THREADS = 256;
 constexpr int DIAG_WORDS = 11;    // per-block diagnostics partial
 

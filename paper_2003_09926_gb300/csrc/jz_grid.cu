@@ -712,10 +712,23 @@ __global__ void k_pack(Layout L, const ST* __restrict__ Q, const double* __restr
   }
 }
 
+// one metric field f (S^k_m at 3k+m, J at 9) of the grid's own nodes, widened
+template <typename MT>
+__global__ void k_pack_metric(Layout L, const MT* __restrict__ M, int f, double* __restrict__ dense) {
+  const long long N = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.n[0]);
+    const int j = (int)((t / L.n[0]) % L.n[1]);
+    const int k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    dense[t] = (double)M[(long long)f * L.npad + L.at(i, j, k)];
+  }
+}
+
 int grid_blocks(long long work, int threads) {
   long long b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > 152LL * 32) b = 152LL * 32;
+  const long long cap = 32LL * device_sm_count();
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -889,6 +902,16 @@ cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s)
     k_unpack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (double*)g.Q0, nullptr);
   else
     k_unpack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, dense, (float*)g.Q0, g.Q0d);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_metric(const GridDev& g, int f, double* dense, cudaStream_t s) {
+  const long long N = (long long)g.L.n[0] * g.L.n[1] * g.L.n[2];
+  if (g.prec == JZ_P64 || g.prec == JZ_P32_M64)
+    k_pack_metric<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.M, f, dense);
+  else
+    k_pack_metric<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.M, f, dense);
   count_launches(1);
   return cudaGetLastError();
 }

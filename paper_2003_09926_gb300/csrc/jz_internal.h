@@ -30,6 +30,7 @@ struct GridDev {
   int goff[3], gn[3];  // global index of local node 0 and global node counts (blocks; else 0 and n)
   int variant;         // stage kernel of P32: 0 scalar records, 2 vector records
   int vti, vtj;        // tile shape of the vector-record kernel (32 x 16, 16 x 32 or 16 x 16)
+  int stall_test;      // test only: the stage kernels' copies wait for bytes that nothing delivers
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
   CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)
@@ -64,6 +65,8 @@ cudaError_t launch_init(const GridDev& g, uint64_t seed, cudaStream_t s);
 cudaError_t launch_bc(const GridDev& g, void* Q, cudaStream_t s, bool full = false);
 cudaError_t launch_unpack(const GridDev& g, const double* dense, cudaStream_t s);
 cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s);
+// one metric field (S^k_m at 3k+m, J at 9) of the grid's own nodes, widened to FP64
+cudaError_t launch_pack_metric(const GridDev& g, int f, double* dense, cudaStream_t s);
 
 // batched boundary fill over a device table of per-grid contexts
 size_t bc_ctx_bytes();
@@ -110,6 +113,8 @@ inline StageTiling grid_tiling(const GridDev& g) {
   return (g.prec == JZ_P32 && g.variant == 2) ? StageTiling{g.vti, g.vtj} : stage_tiling(g.prec);
 }
 int stage_ctas_per_sm(int prec);
+// streaming multiprocessors of the current device (queried once per device)
+int device_sm_count();
 // qsel / qout select the input state Q^(l-1) and the output Q^(l): 0 = Q0, 1 = QA, 2 = QB
 cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaStream_t s);
 // batched stage: a device table of per-grid stage contexts and work items

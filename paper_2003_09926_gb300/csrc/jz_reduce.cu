@@ -24,8 +24,10 @@ namespace {
 // fit leave the last wave partly idle (diagnostics of the 256x192x192 FP32
 // grid: 0.086 ms with 456 blocks, 0.110 ms with 1216).  Both fit the
 // RED_BLOCKS partials.
-constexpr int DIAG_GRID = 3 * 152, RATE_GRID = 2 * 152;
-static_assert(DIAG_GRID <= RED_BLOCKS && RATE_GRID <= RED_BLOCKS, "partials");
+int red_grid(int per_sm) {
+  const int b = per_sm * device_sm_count();
+  return b < RED_BLOCKS ? b : RED_BLOCKS;
+}
 
 template <typename T>
 __device__ __forceinline__ T sutherland(T mu_inf, T s1, T temp) {
@@ -330,15 +332,15 @@ cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaS
   }
   switch (g.prec) {
     case JZ_P64:
-      k_timestep<double, double><<<RATE_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
+      k_timestep<double, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
                                                                     (const double*)g.M, g.sc, g.partial, cfl);
       break;
     case JZ_P32_M64:
-      k_timestep<float, double><<<RATE_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
+      k_timestep<float, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
                                                                    (const double*)g.M, g.sc, g.partial, cfl);
       break;
     default:
-      k_timestep<float, float><<<RATE_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
+      k_timestep<float, float><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
                                                                   g.sc, g.partial, cfl);
       break;
   }
@@ -378,15 +380,15 @@ cudaError_t launch_timestep_batch(int prec, const void* ctx, int n, double cfl, 
 cudaError_t launch_diagnostics(const GridDev& g, cudaStream_t s) {
   switch (g.prec) {
     case JZ_P64:
-      k_diag<double, double><<<DIAG_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0, (const double*)g.M,
+      k_diag<double, double><<<red_grid(3), RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0, (const double*)g.M,
                                                                 g.sc, g.partial);
       break;
     case JZ_P32_M64:
-      k_diag<float, double><<<DIAG_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const double*)g.M,
+      k_diag<float, double><<<red_grid(3), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const double*)g.M,
                                                                g.sc, g.partial);
       break;
     default:
-      k_diag<float, float><<<DIAG_GRID, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M, g.sc,
+      k_diag<float, float><<<red_grid(3), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M, g.sc,
                                                               g.partial);
       break;
   }

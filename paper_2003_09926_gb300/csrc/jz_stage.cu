@@ -249,6 +249,8 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
   const int t0 = L.lo[2] + bz * X.kc;
   const int t1 = min(t0 + X.kc, L.hi[2] + 1);
   const int pbase = t0 - 2;  // first staged plane
+  const uint32_t xtx = st.stall ? kStallBytes : 0u;
+  const long long wlim = st.stall ? kStallLimit : kWaitLimit;
 
   // node-pass role of this thread: tile node, j-halo node or i-halo node
   int nx, ny, role;
@@ -266,7 +268,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
       const int b = (p - pbase) & 1;
       ++issued[b];
       fence_async_shared();
-      mbar_expect_tx(&bar[b], C::RAW_TX);
+      mbar_expect_tx(&bar[b], C::RAW_TX + xtx);
       tma_load_4d(raw[b], &X.tmQ[st.qin], &bar[b], i0, j0, p + NG, 0);
     }
   };
@@ -274,7 +276,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
     if (tid == 0) {
       ++issued[2];
       fence_async_shared();
-      mbar_expect_tx(&bar[2], C::MET_TX);
+      mbar_expect_tx(&bar[2], C::MET_TX + xtx);
       tma_load_4d(met, &X.tmM, &bar[2], i0, j0, p + NG, 0);
     }
   };
@@ -286,7 +288,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
     }
   };
   auto wait_bar = [&](int b) {
-    const bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1);
+    const bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1, wlim);
     if (!ok && tid == 0) record(b, ph[b] & 1, -100);
     ++ph[b];
     if (ok && tid == 0) ++waited[b];
@@ -314,12 +316,12 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
   // met_plane) with one barrier, convert plane p, then stage plane p + 2
   auto fetch_plane = [&](int p, bool with_met, int met_plane) {
     const int b = (p - pbase) & 1;
-    bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1);
+    bool ok = mbar_wait_bounded(&bar[b], ph[b] & 1, wlim);
     if (!ok && tid == 0) record(b, ph[b] & 1, p);
     ++ph[b];
     if (ok && tid == 0) ++waited[b];
     if (with_met) {
-      const bool okm = ok && mbar_wait_bounded(&bar[2], ph[2] & 1);
+      const bool okm = ok && mbar_wait_bounded(&bar[2], ph[2] & 1, wlim);
       if (ok && !okm && tid == 0) record(2, ph[2] & 1, met_plane);
       ++ph[2];
       if (okm && tid == 0) ++waited[2];
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
   int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};
   bool failed = false;
   stage_item<R, MT, TI, TJ, S64>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
-  if (failed) drain_after_timeout(bar, X.err, issued, waited);
+  if (failed) drain_after_timeout(bar, X.err, issued, waited, st.stall ? kStallBytes : 0u);
 }
 
 // Many grids: persistent CTAs (one per SM) take work items (grid, tile,
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
     stage_item<R, MT, TI, TJ, S64>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
     if (failed) break;
   }
-  if (failed) drain_after_timeout(bar, ctx[gsel].err, issued, waited);
+  if (failed) drain_after_timeout(bar, ctx[gsel].err, issued, waited, st.stall ? kStallBytes : 0u);
 }
 
 // tile shapes per precision (one CTA per SM)
@@ -598,7 +600,7 @@ cudaError_t launch_one(const GridDev& g, int stage, int qsel, int qout, cudaStre
   using Cf = Cfg<R, MT, TI, TJ>;
   StageCtx<R, MT> X;
   fill_ctx(X, g);
-  const StageSel st{kRkAlpha[stage], qsel, qout};
+  const StageSel st{kRkAlpha[stage], qsel, qout, g.stall_test};
   const int nz = g.L.hi[2] - g.L.lo[2] + 1;
   dim3 grid((g.L.hi[0] + TI) / TI, (g.L.hi[1] + TJ) / TJ, (nz + g.kc - 1) / g.kc);
   k_stage<R, MT, TI, TJ, S64><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
@@ -610,10 +612,11 @@ template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue, int stage, int qsel,
                          int qout, cudaStream_t s) {
   using Cf = Cfg<R, MT, TI, TJ>;
-  const StageSel st{kRkAlpha[stage], qsel, qout};
+  const StageSel st{kRkAlpha[stage], qsel, qout, 0};
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  const int ctas = nitems < 152 * Cf::MINB ? nitems : 152 * Cf::MINB;
+  const int slots = device_sm_count() * Cf::MINB;
+  const int ctas = nitems < slots ? nitems : slots;
   k_stage_batch<R, MT, TI, TJ, S64><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
@@ -656,7 +659,7 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
       if (g.variant == 2) {
         StageCtx<float, float> X;
         fill_ctx(X, g);
-        const StageSel st{kRkAlpha[stage], qsel, qout};
+        const StageSel st{kRkAlpha[stage], qsel, qout, g.stall_test};
         if (g.vti == 16 && g.vtj == 32) return launch_stage_v_16x32(X, st, s);
         if (g.vti == 16 && g.vtj == 16) return launch_stage_v_16x16(X, st, s);
         return launch_stage_v_32x16(X, st, s);
@@ -684,7 +687,7 @@ void stage_ctx_fill(void* dst, const GridDev& g) {
 cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const void* ctx, const int4* items,
                                int nitems, unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
   if (prec == JZ_P32 && variant == 2) {
-    const StageSel st{kRkAlpha[stage], qsel, qout};
+    const StageSel st{kRkAlpha[stage], qsel, qout, 0};
     if (tile.ti == 16 && tile.tj == 32) return launch_stage_v_batch_16x32(ctx, items, nitems, queue, st, s);
     if (tile.ti == 16 && tile.tj == 16) return launch_stage_v_batch_16x16(ctx, items, nitems, queue, st, s);
     return launch_stage_v_batch_32x16(ctx, items, nitems, queue, st, s);

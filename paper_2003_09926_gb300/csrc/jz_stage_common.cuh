@@ -108,13 +108,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^31 SM cycles (about a second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM cycles (by default 2^31, about a
+// second).
+constexpr long long kWaitLimit = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitLimit) {
   const long long start = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - start > (1LL << 31)) return false;
+    if (clock64() - start > limit) return false;
   }
   return true;
+}
+
+// Explicit completion of `bytes` transaction bytes on the barrier's current
+// phase (used only by the stall test's recovery, see StageSel::stall).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
 }
 
 // 4-D tiled TMA load: box at (x, y, z, w) of the tensor map into shared memory.
@@ -148,10 +157,18 @@ struct alignas(128) StageCtx {
 };
 
 // Per-launch stage selection: alpha_l, input copy Q^(l-1), output copy Q^(l).
+// stall (test only, 0 otherwise): every TMA copy of the launch expects
+// kStallBytes more than it delivers, so its barrier phase cannot complete,
+// and waits give up after kStallLimit cycles.  The kernel then takes its
+// timeout path: it records the failure, completes the missing bytes itself,
+// waits (default limit) for the real copies to land and returns.
 struct StageSel {
   double alpha;
   int qin, qout;
+  int stall;
 };
+constexpr uint32_t kStallBytes = 16;
+constexpr long long kStallLimit = 1LL << 16;
 
 __device__ __forceinline__ void init_barriers(uint64_t* bar) {
   if (threadIdx.x == 0) {
@@ -164,13 +181,17 @@ __device__ __forceinline__ void init_barriers(uint64_t* bar) {
 }
 
 // after a timeout: record it and let this CTA's copies still in flight land
+// (xtx: the transaction bytes each copy expects beyond what it delivers,
+// nonzero only in the stall test, completed here before the wait)
 __device__ __forceinline__ void drain_after_timeout(uint64_t* bar, int* err, const int issued[3],
-                                                    const int waited[3]) {
+                                                    const int waited[3], uint32_t xtx) {
   if (threadIdx.x == 0) {
     atomicExch(err, 1);
     for (int b = 0; b < 3; ++b)
-      for (int u = waited[b]; u < issued[b]; ++u)
+      for (int u = waited[b]; u < issued[b]; ++u) {
+        if (xtx) mbar_complete_tx(&bar[b], xtx);
         if (!mbar_wait_bounded(&bar[b], u & 1)) break;  // phase u of barrier b
+      }
   }
   __syncthreads();
 }

@@ -121,8 +121,8 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 // bounded wait with a fast path (the copy has normally landed long before)
-__device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity) {
-  return mbar_try_wait(bar, parity) || mbar_wait_bounded(bar, parity);
+__device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity, long long limit) {
+  return mbar_try_wait(bar, parity) || mbar_wait_bounded(bar, parity, limit);
 }
 
 // Node quantities of node (x, y) of plane kk: G^k = E^k - F^k, lambda~^k,
@@ -299,6 +299,8 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   const int t0 = L.lo[2] + bz * X.kc;
   const int t1 = min(t0 + X.kc, L.hi[2] + 1);
   const int pbase = t0 - 2;  // first staged plane
+  const uint32_t xtx = st.stall ? kStallBytes : 0u;
+  const long long wlim = st.stall ? kStallLimit : kWaitLimit;
 
   // node role: tile node, j-halo node (rows -1, TJ) or i-halo node (columns -1, TI)
   int nx, ny, role;
@@ -334,7 +336,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       pend |= 1u << b;
       ppar = (ppar & ~(1u << b)) | (parity << b);
       fence_async_shared();
-      mbar_expect_tx(&sm.bar[b], RAW_TX);
+      mbar_expect_tx(&sm.bar[b], RAW_TX + xtx);
       tma_load_4d(dst, &X.tmQ[st.qin], &sm.bar[b], i0, j0, p + NG, 0);
     }
   };
@@ -343,13 +345,13 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       pend |= 1u << B_MET;
       ppar = (ppar & ~(1u << B_MET)) | ((uint32_t)((p - t0 + 1) & 1) << B_MET);
       fence_async_shared();
-      mbar_expect_tx(&sm.bar[B_MET], MET_TX);
+      mbar_expect_tx(&sm.bar[B_MET], MET_TX + xtx);
       tma_load_4d(sm.met, &X.tmMv, &sm.bar[B_MET], i0, j0 + 1, p + NG, 0);
     }
   };
   bool ok = true;
   auto wait = [&](int b, uint32_t parity, int p) {
-    const bool r = wait_v(&sm.bar[b], parity);
+    const bool r = wait_v(&sm.bar[b], parity, wlim);
     if (tid == 0) {
       if (r) pend &= ~(1u << b);
       else if (atomicCAS(X.err, 0, 1) == 0) {
@@ -500,7 +502,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       pend |= 1u << B_Q0;
       ppar = (ppar & ~(1u << B_Q0)) | ((uint32_t)((p - t0) & 1) << B_Q0);
       fence_async_shared();
-      mbar_expect_tx(&sm.bar[B_Q0], Q0_TX);
+      mbar_expect_tx(&sm.bar[B_Q0], Q0_TX + xtx);
       tma_load_4d(smem + O_Q0, &X.tmQ0u, &sm.bar[B_Q0], i0, j0 + 2, p + NG, 0);
     }
   };
@@ -617,7 +619,10 @@ fail:
   if (tid == 0) {
     atomicExch(X.err, 1);
     for (int b = 0; b < NBAR; ++b)
-      if (pend & (1u << b)) mbar_wait_bounded(&sm.bar[b], (ppar >> b) & 1u);
+      if (pend & (1u << b)) {
+        if (xtx) mbar_complete_tx(&sm.bar[b], xtx);
+        mbar_wait_bounded(&sm.bar[b], (ppar >> b) & 1u);
+      }
   }
   __syncthreads();
   return false;
@@ -667,7 +672,8 @@ cudaError_t VR_FN(launch_stage_v_batch)(const void* ctx, const int4* items, int 
                                         const StageSel& st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  const int ctas = nitems < 152 ? nitems : 152;
+  const int sms = device_sm_count();
+  const int ctas = nitems < sms ? nitems : sms;
   k_stage_v_batch<<<ctas, vr::NT, vr::BYTES, s>>>((const StageCtx<float, float>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();

@@ -14,7 +14,6 @@
 // GPU (different streams, no ordering between them) race on it.  Calls on one
 // stream, or otherwise ordered, are safe.
 #include <cmath>
-#include <mutex>
 
 #include "jz_internal.h"
 
@@ -31,10 +30,6 @@ constexpr long long SD_MAX_NODES = SD_CHUNK * SD_MAX_CHUNKS;  // 268,435,456
 // per-block partial records, then one word for the last-block counter
 // (4096 x 11 x 8 bytes + 256 bytes, about 352 KB per device)
 static __device__ __align__(256) double sd_scratch[SD_MAX_CHUNKS * SD_WORDS + 32];
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[MAX_DEVICES] = {nullptr};
 
 template <typename ST>
 __global__ void __launch_bounds__(SD_THREADS) k_diag_static(long long n, const ST* __restrict__ Q,
@@ -106,7 +101,6 @@ __global__ void __launch_bounds__(SD_THREADS) k_diag_static(long long n, const S
     }
     for (int c = 0; c < SD_WORDS; ++c) out[c] = r[c];
     out[9] = sqrt(r[9]);  // maximum Mach number
-    *counter = 0;
   }
 }
 
@@ -125,24 +119,19 @@ extern "C" int jz_state_diagnostics_static(long long n_nodes, int fp64, const vo
   if (!Q || !vol || !out) return static_fail(JZ_EINVAL, "null device pointer");
   if (fp64 != 0 && fp64 != 1) return static_fail(JZ_EINVAL, "fp64 must be 0 or 1");
   if (!(gamma > 1.0)) return static_fail(JZ_EINVAL, "gamma must exceed 1");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
-    return static_fail(JZ_ECUDA, "no usable current CUDA device");
-  double* scratch = nullptr;
-  {
-    // one-time set-up per device, with that device current: the host-side
-    // name of the static array is not a device address, so look it up
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, sd_scratch);
-      if (e != cudaSuccess || !p) return static_fail(JZ_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
-      g_scratch_ptr[dev] = (double*)p;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  // The host-side name of the static array is not a device address.  Look
+  // the address up on every call, for the device (and context) current now:
+  // the lookup allocates nothing, and a cached address would go stale once
+  // the device is reset and the library's device code loaded again.  The
+  // first call on a device also loads that device code (lazy loading).
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, sd_scratch);
+  if (e != cudaSuccess || !p) return static_fail(JZ_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
+  double* scratch = (double*)p;
   cudaStream_t s = (cudaStream_t)stream;
-  // the last-block counter must start at zero
+  // The last-block counter must start at zero.  This memset, enqueued ahead
+  // of the kernel on the same stream, is what guarantees it; it also clears
+  // a count left by an earlier call that did not complete.
   if (cudaMemsetAsync(scratch + SD_MAX_CHUNKS * SD_WORDS, 0, sizeof(unsigned int), s) != cudaSuccess)
     return static_fail(JZ_ECUDA, "clearing the static counter failed");
   const long long blocks_ll = n_nodes > 0 ? (n_nodes + SD_CHUNK - 1) / SD_CHUNK : 1;
@@ -152,7 +141,7 @@ extern "C" int jz_state_diagnostics_static(long long n_nodes, int fp64, const vo
   else
     k_diag_static<float><<<blocks, SD_THREADS, 0, s>>>(n_nodes, (const float*)Q, vol, gamma, scratch, out);
   count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(JZ_ECUDA, cudaGetErrorString(e));
   return JZ_OK;
 }

@@ -51,7 +51,8 @@ __global__ void k_stats_axis_x(Layout L, Coords C, int jc, int kc, double* __res
 
 int grid_blocks_s(long long work) {
   long long b = (work + 255) / 256;
-  return (int)(b < 1 ? 1 : (b > 152LL * 32 ? 152LL * 32 : b));
+  const long long cap = 32LL * device_sm_count();
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 }  // namespace

@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
             "jz_diagnostics_async": ([G, VP], C.c_int),
             "jz_state_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_state_upload": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
+            "jz_metrics_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_batch_bytes": ([C.POINTER(G), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
             "jz_batch_create": ([C.POINTER(G), C.c_int, VP, C.c_size_t, VP, C.POINTER(B)], C.c_int),
             "jz_batch_nsteps": ([B, C.c_int, C.c_double], C.c_int),
@@ -98,6 +99,7 @@ def lib() -> C.CDLL:
             "jz_get_tiling": ([G, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "jz_set_tiling": ([G, C.c_int], C.c_int),
             "jz_set_stage_variant": ([G, C.c_int], C.c_int),
+            "jz_set_stall_test": ([G, C.c_int], C.c_int),
             "jz_set_tile_shape": ([G, C.c_int, C.c_int], C.c_int),
             "jz_fma_peak": ([C.c_int, C.POINTER(C.c_double), VP], C.c_int),
         }
@@ -234,6 +236,12 @@ def jz_state_download(h, out: np.ndarray) -> np.ndarray:
     return out
 
 
+def jz_metrics_download(h, out: np.ndarray) -> np.ndarray:
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    _check(lib().jz_metrics_download(h, out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
+    return out
+
+
 def jz_state_upload(h, Q: np.ndarray) -> None:
     Q = np.ascontiguousarray(Q, dtype=np.float64)
     _check(lib().jz_state_upload(h, Q.ctypes.data_as(C.POINTER(C.c_double)), Q.size))
@@ -272,6 +280,10 @@ def jz_set_tiling(h, kc: int) -> None:
 
 def jz_set_stage_variant(h, variant: int) -> None:
     _check(lib().jz_set_stage_variant(h, variant))
+
+
+def jz_set_stall_test(h, on: bool) -> None:
+    _check(lib().jz_set_stall_test(h, int(bool(on))))
 
 
 def jz_set_tile_shape(h, ti: int, tj: int) -> None:
@@ -349,6 +361,10 @@ class Grid:
         if out is None:
             out = np.empty(self.shape)
         return jz_state_download(self.h, out)
+
+    def metrics(self) -> np.ndarray:
+        """[10][nk][nj][ni] FP64: S^k_m at 3k+m, J at 9."""
+        return jz_metrics_download(self.h, np.empty((10,) + tuple(self.shape[1:])))
 
     def upload(self, Q: np.ndarray):
         assert Q.shape == self.shape

@@ -84,3 +84,35 @@ def test_autotuner_chooses_shape_and_chunk(jz):
         np.testing.assert_array_equal(a, c)
     one = autotune.tune_grid(cases[0][0], cases[0][1])
     assert one["shape"] in autotune.SHAPES
+
+
+def _rel_err(got, ref):
+    return max(np.abs(got[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(5))
+
+
+def test_p64_batch_matches_the_oracle(jz):
+    """Direct parity of the batched path: three uneven FP64 jet grids (one
+    with the sinusoidal mapping, one chunked in k), each with its own Mach
+    and Reynolds numbers and its own CFL time step, advanced five steps in
+    one batch, are each within 1e-10 of the CPU oracle run on that grid
+    alone (paper Section 4.2, Fig. jazzy: the per-stage sequence)."""
+    import torch
+
+    import oracle
+    stream = torch.cuda.Stream()
+    cases = [(W.jet_grid(40, 24, 20, map_amp=0.03, map_seed=5), W.jet_flow(mach=1.3, re=8e5), 11),
+             (W.jet_grid(33, 17, 19), W.jet_flow(mach=1.9, re=1.5e6), 12),
+             (W.jet_grid(20, 28, 14, map_amp=0.02, map_seed=2), W.jet_flow(mach=1.5, re=2e4), 13)]
+    grids = [jz.Grid(g, stream=stream).init(f, s) for g, f, s in cases]
+    jz.jz_set_tiling(grids[0].h, 3)
+    b = jz.Batch(grids, stream=stream)
+    b.nsteps(5, cfl=0.5)
+    stream.synchronize()
+    for (gd, f, s), g in zip(cases, grids):
+        o = oracle.Oracle(gd, f)
+        Q = o.init(s)
+        o.run(Q, 5, cfl=0.5)
+        err = _rel_err(g.download(), o.inner(Q))
+        assert err <= 1e-10, (gd["ni"], gd["nj"], gd["nk"], err)
+        assert g.diagnostics()["time"] == pytest.approx(o.time, rel=1e-12)
+    b.close()

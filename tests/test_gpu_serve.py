@@ -59,3 +59,29 @@ def test_over_budget_request_rejected(mods):
     res = srv.run(reqs)
     assert res[0].status.startswith("rejected")
     assert all(r.status == "done" for r in res[1:] if jz.jz_grid_bytes(reqs[r.rid].grid) < need)
+
+
+def test_served_p64_cases_match_the_oracle(mods):
+    """Direct parity of the serving path: FP64 cases arriving at different
+    times, served under a budget that holds two of them, advanced in
+    slices mixed with each other, are each within 1e-10 of the CPU oracle
+    run on that case alone."""
+    import oracle
+    jz, serve = mods
+    shapes = [(30, 20, 16), (24, 18, 20), (36, 16, 14), (20, 20, 20)]
+    reqs = []
+    for i, sh in enumerate(shapes):
+        flow = W.jet_flow(mach=1.3 + 0.15 * i, re=4e5 * (i + 1))
+        reqs.append(serve.Request(i, W.jet_grid(*sh, map_amp=0.02 * (i % 2), map_seed=i, precision=W.P64), flow,
+                                  70 + i, 6 + 2 * i, 0.01 * i))
+    sizes = sorted(jz.jz_grid_bytes(r.grid) for r in reqs)
+    srv = serve.Server(sizes[-1] + sizes[-2], slice_steps=3, keep_state=True)
+    res = srv.run(reqs)
+    assert all(r.status == "done" for r in res) and srv.slices >= 4
+    for r, q in zip(res, reqs):
+        o = oracle.Oracle(q.grid, q.flow)
+        Q = o.init(q.seed)
+        o.run(Q, q.steps, cfl=0.5)
+        ref = o.inner(Q)
+        err = max(np.abs(r.state[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(5))
+        assert err <= 1e-10, (q.rid, err)
