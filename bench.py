@@ -260,15 +260,28 @@ def host_cpu() -> dict:
 # reading R8): 0 supersonic inflow (u_n <= -c), 1 subsonic with the outside
 # entropy, 2 subsonic with the inside entropy, 3 supersonic outflow
 # (u_n >= c); the subsonic split is the sign of the characteristic average
-# u_n + 2 (c - c_inf) / (gamma - 1) against air at rest (c_inf = 1).
-def riemann_branch(q, n, gamma=1.4):
+# u_n + 2 (c - c_inf) / (gamma - 1) against air at rest (c_inf = 1).  With
+# margin=True also returns the distance of the state to the nearest of the
+# three switches (|u_n - c|, |u_n + c|, |u_n + 2 (c - 1)/(gamma - 1)|).
+def riemann_branch(q, n, gamma=1.4, margin=False):
     rho = q[0]
     u = q[1:4] / rho
     p = (gamma - 1.0) * (q[4] - 0.5 * rho * (u * u).sum(axis=0))
     c = np.sqrt(gamma * p / rho)
     un = (u * n).sum(axis=0)
-    sub_out = un + 2.0 * (c - 1.0) / (gamma - 1.0) > 0.0
-    return np.where(un >= c, 3, np.where(un <= -c, 0, np.where(sub_out, 2, 1)))
+    split = un + 2.0 * (c - 1.0) / (gamma - 1.0)
+    br = np.where(un >= c, 3, np.where(un <= -c, 0, np.where(split > 0.0, 2, 1)))
+    if margin:
+        return br, np.minimum(np.minimum(np.abs(un - c), np.abs(un + c)), np.abs(split))
+    return br
+
+
+# Far-field face nodes closer than this (in velocity units, c_inf = 1) to a
+# branch switch in either state are counted as "near a switch": the FP32
+# kernel takes the branch decision in its own arithmetic, where 5c - 5 and
+# u_n carry errors of a few 1e-6, and the FP32 state at the adjacent node
+# differs from the FP64 one by about 1e-5 in these quantities.
+BRANCH_MARGIN = 2e-4
 
 
 def error_classes(Q, Qref, S, bc, gamma=1.4):
@@ -276,8 +289,10 @@ def error_classes(Q, Qref, S, bc, gamma=1.4):
     far-field face nodes whose Riemann branch (riemann_branch, from the
     adjacent interior node and the outward unit normal S^k/|S^k| of the face
     that sets the node: later faces in the order y-, y+, z-, z+, x+, x- win)
-    is the same in both states, and those where it differs; nodes at distance
-    1, 2 and >= 3 from the nearest non-periodic face.  Q, Qref: [5][nk][nj][ni];
+    is the same in both states and at least BRANCH_MARGIN from every switch,
+    and the others (near a switch, where the two precisions may decide
+    differently); nodes at distance 1, 2 and >= 3 from the nearest
+    non-periodic face.  Q, Qref: [5][nk][nj][ni];
     S: [>= 9][nk][nj][ni] metrics; bc: the six face kinds (0 periodic, 1
     inflow, 2 far field).  Error of a class: max over variables of
     max|Q - Qref| over its nodes / max|Qref| over all nodes."""
@@ -325,12 +340,12 @@ def error_classes(Q, Qref, S, bc, gamma=1.4):
         sg = -1.0 if f % 2 == 0 else 1.0
         nv = np.stack([S[3 * d + e][kk, jj, ii] for e in range(3)])
         nv = sg * nv / np.sqrt((nv * nv).sum(axis=0))
-        b32 = riemann_branch(Q[:, ci[2], ci[1], ci[0]], nv, gamma)
-        b64 = riemann_branch(Qref[:, ci[2], ci[1], ci[0]], nv, gamma)
+        b32, m32 = riemann_branch(Q[:, ci[2], ci[1], ci[0]], nv, gamma, margin=True)
+        b64, m64 = riemann_branch(Qref[:, ci[2], ci[1], ci[0]], nv, gamma, margin=True)
         ff[kk, jj, ii] = True
-        differs[kk, jj, ii] = b32 != b64
-    out["farfield_face_same_branch"] = stat(ff & ~differs)
-    out["farfield_face_branch_differs"] = stat(ff & differs)
+        differs[kk, jj, ii] = (b32 != b64) | (np.minimum(m32, m64) < BRANCH_MARGIN)
+    out["farfield_face_clear_of_switch"] = stat(ff & ~differs)
+    out["farfield_face_near_switch"] = stat(ff & differs)
     out["interior_d1"] = stat(dist == 1)
     out["interior_d2"] = stat(dist == 2)
     out["interior_d3plus"] = stat(dist >= 3)
@@ -752,7 +767,7 @@ def main(argv=None):
             "variants": {W.PRECISION_NAMES[p]: r for p, r in results.items()},
             "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
                                    "interior": "nodes at least 3 from every face",
-                                   "classes": "every node by class: inflow face; far-field face nodes whose Riemann branch (supersonic in / subsonic outside entropy / subsonic inside entropy / supersonic out, from the adjacent interior node) is the same in both precisions, and those where it differs; nodes at distance 1, 2 and >= 3 from the nearest face"},
+                                   "classes": "every node by class: inflow face; far-field face nodes whose Riemann branch (supersonic in / subsonic outside entropy / subsonic inside entropy / supersonic out, from the adjacent interior node) is the same in both precisions and at least 2e-4 from every switch, and the others (near a switch: the two precisions may decide differently); nodes at distance 1, 2 and >= 3 from the nearest face"},
             "fp64_vs_fp32_speedup": results[head]["value"] / results[W.P64]["value"]}
     if not args.no_batched:
         line["batched"] = bench_batched(jz, torch, W, local, steps=max(10, args.steps // 5), steps64=2)

@@ -194,15 +194,16 @@ def test_fp32_modes_error_bound_config0(jz, orc):
         print(prec, variant, {k: (v["nodes"], v["max_rel"]) for k, v in cls.items()})
         for name, bound in FP32_CLASS_BOUNDS.items():
             assert cls[name]["max_rel"] <= bound, (prec, variant, name, cls[name])
-        faces = cls["farfield_face_same_branch"]["nodes"] + cls["farfield_face_branch_differs"]["nodes"]
-        assert cls["farfield_face_branch_differs"]["nodes"] <= 0.02 * faces, cls["farfield_face_branch_differs"]
+        faces = cls["farfield_face_clear_of_switch"]["nodes"] + cls["farfield_face_near_switch"]["nodes"]
+        assert cls["farfield_face_near_switch"]["nodes"] <= 0.02 * faces, cls["farfield_face_near_switch"]
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
 # FP32 bound of each node class after 20 steps of the 48x32x32 jet (max error
 # relative to max|v| over the grid, worst conserved variable)
-FP32_CLASS_BOUNDS = {"interior_d3plus": 2e-3, "interior_d2": 1e-2, "interior_d1": 1e-2, "inflow_face": 1e-5,
-                     "farfield_face_same_branch": 1e-2, "farfield_face_branch_differs": 0.5}
+# (measured on a GB300: 1.5e-5, 1.8e-4, 6.0e-4, 4.8e-8, 2.7e-4, no branch flips)
+FP32_CLASS_BOUNDS = {"interior_d3plus": 1e-4, "interior_d2": 1e-3, "interior_d1": 2e-3, "inflow_face": 1e-6,
+                     "farfield_face_clear_of_switch": 1e-3, "farfield_face_near_switch": 0.5}
 
 
 def test_metrics_download_matches_the_oracle(jz, orc):
@@ -213,12 +214,16 @@ def test_metrics_download_matches_the_oracle(jz, orc):
     o = orc.Oracle(grid, W.jet_flow())
     want = np.concatenate([o.inner(o.S), o.inner(o.J)[None]])
     scale = np.abs(want).reshape(10, -1).max(axis=1)[:, None, None, None]
-    for prec, tol in ((W.P64, 1e-12), (W.P32, 2.0 ** -23)):
+    # FP64: both sides form the same differences in a different operation
+    # order (cancellation in the off-diagonal terms), so the bound is
+    # relative to each field's largest value; FP32 adds the rounding to FP32
+    for prec, rel in ((W.P64, 0.0), (W.P32, 2.0 ** -24)):
         g = jz.Grid(dict(grid, precision=prec)).init(W.jet_flow(), 0)
         got = g.metrics()
         g.close()
         assert got.shape == want.shape
-        assert np.all(np.abs(got - want) <= tol * np.maximum(np.abs(want), 1e-3 * scale)), prec
+        err = np.abs(got - want) - rel * np.abs(want)
+        assert np.all(err <= 1e-12 * scale), (prec, (err / scale).max())
 
 
 @pytest.mark.parametrize("shape,amp", [((37, 29, 23), 0.05), ((48, 32, 32), 0.0)])
