@@ -375,9 +375,10 @@ int jz_set_stage_variant(jz_grid* g, int variant);
 int jz_set_stall_test(jz_grid* g, int on);
 
 /* Tile shape (ti x tj nodes in i and j) of the FP32 vector-record stage
- * kernel of this grid: 32 x 16 (default), 16 x 32 or 16 x 16, each a build of
- * the same kernel (one CTA per SM; 16 x 32 wastes less of a tile on grids
- * narrow in i, 16 x 16 on small grids).  The per-node arithmetic does not
+ * kernel of this grid: 16 x 16 (default), 32 x 16 or 16 x 32, each a build of
+ * the same kernel (16 x 16 runs two CTAs per SM, the others one; 16 x 16
+ * also wastes least of a tile on small grids, 16 x 32 on grids narrow in
+ * i).  The per-node arithmetic does not
  * depend on the shape: results are bitwise the same.  Resets the k-chunk
  * length to its default for the shape.  A batch needs one shape for all its
  * grids.  JZ_EINVAL for another shape or for a grid that does not run the

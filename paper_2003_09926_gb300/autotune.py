@@ -1,8 +1,9 @@
 """Autotuner for the stage kernel's tile.
 
 The FP32 vector-record stage kernel is built for three (i, j) tile shapes,
-32 x 16, 16 x 32 and 16 x 16 nodes (one CTA per SM each; the shared memory
-of a CTA is sized for its tile), and the third tile dimension, the number of
+32 x 16, 16 x 32 and 16 x 16 nodes (the shared memory of a CTA is sized for
+its tile: one CTA per SM for the first two, two for 16 x 16, the default),
+and the third tile dimension, the number of
 k-planes a CTA marches through (kc), is free.  Short chunks balance load
 across SMs, long chunks amortise each chunk's prologue (four staged planes
 and two node passes); a narrow tile wastes fewer padded columns on a grid

@@ -284,10 +284,10 @@ int check_dt(double cfl, double dt_fixed) {
 }
 
 // planes per CTA chunk: minimise (waves of resident CTAs) x (planes + prologue)
-int default_kc(const Layout& L, StageTiling t, int prec) {
+int default_kc(const Layout& L, StageTiling t, int ctas_per_sm) {
   long long tiles = (long long)((L.hi[0] + t.ti) / t.ti) * ((L.hi[1] + t.tj) / t.tj);
   int nz = L.hi[2] - L.lo[2] + 1;
-  long long slots = (long long)device_sm_count() * stage_ctas_per_sm(prec);
+  long long slots = (long long)device_sm_count() * ctas_per_sm;
   int best = nz;
   double best_cost = 1e300;
   for (int kc = 1; kc <= nz; ++kc) {
@@ -319,14 +319,18 @@ int make_plane_map(CUtensorMap* m, void* base, bool fp64, const Layout& L, int f
   auto enc = tensor_map_encoder();
   if (!enc) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   const size_t es = fp64 ? 8 : 4;
-  cuuint64_t dims[4] = {(cuuint64_t)L.pitch, (cuuint64_t)(L.n[1] + 2 * NG), (cuuint64_t)(L.n[2] + 2 * NG),
+  // x extent: the row's nodes from ghost -2 to ghost n+1, not the padded
+  // pitch, so that a tile box reaching past the grid's last ghost column
+  // (ragged tiles of narrow grids) is zero-filled instead of fetching the
+  // row padding from memory
+  cuuint64_t dims[4] = {(cuuint64_t)(L.n[0] + 2 * NG), (cuuint64_t)(L.n[1] + 2 * NG), (cuuint64_t)(L.n[2] + 2 * NG),
                         (cuuint64_t)fields};
   cuuint64_t strides[3] = {(cuuint64_t)L.pitch * es, (cuuint64_t)L.plane * es, (cuuint64_t)L.npad * es};
   cuuint32_t box[4] = {(cuuint32_t)(t.ti + 4), (cuuint32_t)(t.tj + 2 * halo_rows), 1, (cuuint32_t)fields};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(JZ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return JZ_OK;
 }
@@ -439,9 +443,9 @@ int create_grid(const jz_grid_desc* desc, const int* o0, const int* o1, void* de
   d.inflow = (double*)(g->base + cv.off_inflow);
   d.axis = (double*)(g->base + cv.off_axis);
   d.variant = d.prec == JZ_P32 ? 2 : 0;  // P32: the vector-record kernel (fastest measured)
-  d.vti = 32;
+  d.vti = 16;  // two CTAs per SM; as fast as 32 x 16 on 256x192x192, faster on small grids
   d.vtj = 16;
-  d.kc = default_kc(cv.L, grid_tiling(d), d.prec);
+  d.kc = default_kc(cv.L, grid_tiling(d), grid_ctas_per_sm(d));
   const int gn[3] = {desc->ni, desc->nj, desc->nk};
   for (int a = 0; a < 3; ++a) {
     d.goff[a] = g->o0[a];
@@ -752,7 +756,7 @@ int jz_set_tile_shape(jz_grid* g, int ti, int tj) {
     return fail(JZ_EINVAL, "tile shape %d x %d is not one of 32 x 16, 16 x 32, 16 x 16", ti, tj);
   g->dev.vti = ti;
   g->dev.vtj = tj;
-  g->dev.kc = default_kc(g->dev.L, grid_tiling(g->dev), g->dev.prec);
+  g->dev.kc = default_kc(g->dev.L, grid_tiling(g->dev), grid_ctas_per_sm(g->dev));
   drop_graph(g);
   return build_maps(g->dev);
 }
@@ -779,8 +783,13 @@ struct BatchPlan {
   int xbegin[3] = {0, 0, 0}, xcount[3] = {0, 0, 0}, xblocks = 1;
 };
 
-// Work items (grid, tile x, tile y, k-chunk) of every grid, largest first,
-// and the layout of the batch's device tables.
+// Work items (grid, tile x, tile y, k-chunk) of every grid, and the layout
+// of the batch's device tables.  Grids are queued largest first (total
+// work), and the items of one grid stay together in row-major tile order:
+// CTAs then take neighbouring tiles of a grid at the same time, so the halo
+// rows two tiles share are read from memory once and served from L2 to the
+// second (sorting single items by size scattered a grid's ragged edge tiles
+// to the end of the queue and read their halos twice).
 int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
   if (!grids || n < 1) return fail(JZ_EINVAL, "bad batch arguments");
   int prec = -1;
@@ -795,8 +804,9 @@ int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
     if (grids[k]->dev.variant != grids[0]->dev.variant || u.ti != t.ti || u.tj != t.tj)
       return fail(JZ_EINVAL, "batch grids must share one stage kernel and tile shape");
   }
-  std::vector<std::pair<long long, int4>> work;
+  std::vector<std::pair<long long, std::vector<int4>>> work;  // (grid's total cost, its items)
   for (int k = 0; k < n; ++k) {
+    work.push_back({0, {}});
     const Layout& L = grids[k]->dev.L;
     const int kc = grids[k]->dev.kc;
     const int tx = (L.hi[0] + t.ti) / t.ti, ty = (L.hi[1] + t.tj) / t.tj;
@@ -807,14 +817,14 @@ int batch_plan(jz_grid* const* grids, int n, BatchPlan& P) {
         for (int bx = 0; bx < tx; ++bx) {
           const int ox = std::min(L.hi[0], (bx + 1) * t.ti - 1) - std::max(L.lo[0], bx * t.ti) + 1;
           const int oy = std::min(L.hi[1], (by + 1) * t.tj - 1) - std::max(L.lo[1], by * t.tj) + 1;
-          const long long cost = (long long)(planes + 3) * (ox > 0 ? ox : 0) * (oy > 0 ? oy : 0) + 1;
-          work.push_back({cost, make_int4(k, bx, by, bz)});
+          work.back().first += (long long)(planes + 3) * (ox > 0 ? ox : 0) * (oy > 0 ? oy : 0) + 1;
+          work.back().second.push_back(make_int4(k, bx, by, bz));
         }
     }
   }
   std::stable_sort(work.begin(), work.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   P.items.clear();
-  for (auto& w : work) P.items.push_back(w.second);
+  for (auto& w : work) P.items.insert(P.items.end(), w.second.begin(), w.second.end());
   size_t off = 0;
   P.off_stage = off; off = align256(off + (size_t)n * stage_ctx_bytes(prec));
   P.off_bc = off; off = align256(off + (size_t)n * bc_ctx_bytes());

@@ -113,6 +113,8 @@ inline StageTiling grid_tiling(const GridDev& g) {
   return (g.prec == JZ_P32 && g.variant == 2) ? StageTiling{g.vti, g.vtj} : stage_tiling(g.prec);
 }
 int stage_ctas_per_sm(int prec);
+// resident CTAs per SM of the stage kernel a grid runs
+int grid_ctas_per_sm(const GridDev& g);
 // streaming multiprocessors of the current device (queried once per device)
 int device_sm_count();
 // qsel / qout select the input state Q^(l-1) and the output Q^(l): 0 = Q0, 1 = QA, 2 = QB

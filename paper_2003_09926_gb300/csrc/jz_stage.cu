@@ -632,6 +632,11 @@ int stage_ctas_per_sm(int prec) {
   }
 }
 
+int grid_ctas_per_sm(const GridDev& g) {
+  if (g.prec == JZ_P32 && g.variant == 2) return vr_ctas_per_sm(g.vti, g.vtj);
+  return stage_ctas_per_sm(g.prec);
+}
+
 StageTiling stage_tiling(int prec) {
   if (prec == JZ_P64) return {TI64, TJ64};
   if (prec == JZ_P32_M64) return {TIM, TJM};

@@ -200,6 +200,11 @@ constexpr double kRkAlpha[5] = {1.0 / 4.0, 1.0 / 6.0, 3.0 / 8.0, 1.0 / 2.0, 1.0}
 
 }  // namespace stg
 
+// CTAs per SM of the FP32 vector-record kernel for a tile shape: tiles of at
+// most 256 nodes (16 x 16) run two CTAs per SM (320 threads, <= 113 KB of
+// shared memory each), larger tiles one
+constexpr int vr_ctas_per_sm(int ti, int tj) { return ti * tj <= 256 ? 2 : 1; }
+
 // FP32 kernel with vector node records (jz_stage_v.cu, one build per tile shape)
 #define JZ_STAGE_V_DECL(S)                                                                                    \
   cudaError_t stage_v_configure_##S();                                                                        \

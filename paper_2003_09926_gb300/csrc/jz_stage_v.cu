@@ -52,6 +52,7 @@ namespace {
 
 namespace vr {
 constexpr int TI = VR_TI, TJ = VR_TJ;
+constexpr int MINB = vr_ctas_per_sm(TI, TJ);    // CTAs per SM
 constexpr int NTILE = TI * TJ;                  // tile nodes
 constexpr int NJH = 2 * TI, NIH = 2 * TJ;       // j-halo (rows -1, TJ) and i-halo (columns -1, TI) nodes
 constexpr int NT = NTILE + NJH + NIH;           // threads (608 for 32 x 16 and 16 x 32)
@@ -62,13 +63,21 @@ constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 3
 // ring records: rows padded to 37 so that the column-wise accesses of the
 // i-halo warp fall on distinct banks
 constexpr int RR = RW + 1, RPL = RR * RH;
-constexpr int NS = 4;                           // ring depth (planes)
-constexpr int GIW = TI + 3, GJH = TJ + 2;       // node buffers: columns -1..TI (padded) / rows -1..TJ
-constexpr int HIW = TI + 3, HJH = TJ + 1;       // face buffers: i faces 0..TI (padded) / j faces 0..TJ
+// ring depths (planes): conserved records 4 (the k face t + 1/2 reads
+// planes t-1 .. t+2), primitive records 3 (the node pass of plane t reads
+// planes t-1 .. t+1)
+constexpr int NSQ = 4, NSP = 3;
+// node buffers: columns -1..TI / rows -1..TJ; face buffers: i faces 0..TI /
+// j faces 0..TJ.  The i-direction rows are padded by one (distinct banks for
+// the i-halo warp's column accesses) except in the two-CTA build, which
+// needs the bytes.
+constexpr int IPAD = MINB > 1 ? 0 : 1;
+constexpr int GIW = TI + 2 + IPAD, GJH = TJ + 2;
+constexpr int HIW = TI + 2 + IPAD, HJH = TJ + 1;
 constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
 constexpr size_t RAW_B = al(4 * 5 * PL);
-constexpr size_t QV_B = al(16 * NS * RPL), QE_B = al(4 * NS * RPL);
-constexpr size_t PV_B = al(16 * NS * RPL), PP_B = al(4 * NS * RPL);
+constexpr size_t QV_B = al(16 * NSQ * RPL), QE_B = al(4 * NSQ * RPL);
+constexpr size_t PV_B = al(16 * NSP * RPL), PP_B = al(4 * NSP * RPL);
 constexpr size_t MET_B = al(4 * 10 * MPL);
 constexpr int UPL = RW * TJ;                     // Q^(0) box: tile rows, 36 columns
 constexpr size_t Q0_B = al(4 * 5 * UPL);
@@ -101,6 +110,9 @@ constexpr size_t BYTES = O_BAR + 128;
 constexpr size_t O_SCR = O_GI4;
 static_assert(O_BAR - O_SCR >= 3 * RAW_B, "prologue staging does not fit");
 static_assert(BYTES <= 232448, "shared memory");
+// two CTAs per SM: 228 KB per SM, 1 KB reserved per CTA, a few bytes of
+// static shared memory in the batched kernel
+static_assert(MINB == 1 || 2 * (BYTES + 128 + 1024) <= 228 * 1024, "two CTAs per SM do not fit");
 constexpr uint32_t RAW_TX = 4 * 5 * PL;
 constexpr uint32_t MET_TX = 4 * 10 * MPL;
 constexpr uint32_t Q0_TX = 4 * 5 * UPL;
@@ -128,11 +140,11 @@ __device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity, long long
 // Node quantities of node (x, y) of plane kk: G^k = E^k - F^k, lambda~^k,
 // nu^k.  Primitive records of the planes below / at / above in slots sM, sC,
 // sP; the conserved record of the plane in slot qC.  DIR = 0: all three
-// directions; DIR = 1 / 2: direction i / j only.
+// directions; DIR = 1 / 2 / 3: direction i / j / k only.
 template <int DIR>
 __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const float* __restrict__ PP,
                                        const float4* __restrict__ QV, const float* __restrict__ QE,
-                                       const float* __restrict__ met, int sM, int sC, int sP, int x, int y,
+                                       const float* __restrict__ met, int sM, int sC, int sP, int qC, int x, int y,
                                        const KConst<float>& c, float G[3][5], float lt[3], float nu[3], float& Jn) {
   using namespace vr;
   const int o = (y + 2) * RR + x + 2;
@@ -145,9 +157,9 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
   const float4 r0 = pc[o];
   const float u = r0.x, v = r0.y, w = r0.z, T = r0.w;
   const float p = PP[sC + o];
-  const float rho = QV[sC + o].x;
-  const float e = QE[sC + o];
-  constexpr int K0 = DIR == 0 ? 0 : DIR - 1;
+  const float rho = QV[qC + o].x;
+  const float e = QE[qC + o];
+  constexpr int K0 = DIR == 0 ? 0 : DIR - 1;  // DIR 3: direction k only
   constexpr int K1 = DIR == 0 ? 3 : DIR;
 
   float Fv[3][4];  // viscous flux vectors F_m (m = x, y, z), components 1..4
@@ -361,16 +373,17 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     }
     ok = ok && r;
   };
-  // ring slot of plane p (both rings): (p - pbase) mod 4
-  auto slot = [&](int p) { return ((p - pbase) & (NS - 1)) * RPL; };
+  // ring slots of plane p: conserved (p - pbase) mod 4, primitive mod 3
+  auto slot = [&](int p) { return ((p - pbase) & (NSQ - 1)) * RPL; };
+  auto pslot = [&](int p) { return ((p - pbase) % NSP) * RPL; };
 
-  // convert staged plane p (planar, in src) into the ring records
-  auto convert = [&](const float* src, int p) {
-    const int s = slot(p);
-    float4* qv = sm.QV + s;
-    float* qe = sm.QE + s;
-    float4* pv = sm.PV + s;
-    float* pp = sm.PP + s;
+  // convert staged plane p (planar, in src) into the ring records: the
+  // conserved record (CQ) and / or the primitive record (CP)
+  auto convert_parts = [&](const float* src, int p, bool CQ, bool CP) {
+    float4* qv = sm.QV + slot(p);
+    float* qe = sm.QE + slot(p);
+    float4* pv = sm.PV + pslot(p);
+    float* pp = sm.PP + pslot(p);
     // halo threads (lighter in the node pass) take three elements each, tile
     // threads one or none
     const int e0 = tid < NTILE ? NCH + tid : tid - NTILE;
@@ -381,21 +394,26 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       const float u = q1 * ri, v = q2 * ri, w = q3 * ri;
       const float pr = c.gm1 * (q4 - 0.5f * q0 * (u * u + v * v + w * w));
       const int r = e + e / RW;  // padded ring row
-      qv[r] = make_float4(q0, q1, q2, q3);
-      qe[r] = q4;
-      pv[r] = make_float4(u, v, w, c.gamma * pr * ri);
-      pp[r] = pr;
+      if (CQ) {
+        qv[r] = make_float4(q0, q1, q2, q3);
+        qe[r] = q4;
+      }
+      if (CP) {
+        pv[r] = make_float4(u, v, w, c.gamma * pr * ri);
+        pp[r] = pr;
+      }
     }
   };
+  auto convert = [&](const float* src, int p) { convert_parts(src, p, true, true); };
 
   // node pass for plane kk: i/j node data to shared memory (for the
   // neighbours' faces) and in registers (for this thread's own faces), k data
   // in registers
   auto node_pass = [&](int kk, Own& w, float G3[5], float& lt3, float& nu3, float& Jn) {
-    const int sM = slot(kk - 1), sC = slot(kk), sP = slot(kk + 1);
+    const int sM = pslot(kk - 1), sC = pslot(kk), sP = pslot(kk + 1), qC = slot(kk);
     float G[3][5], lt[3], nu[3];
     if (role == 0) {
-      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jn);
+      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         w.Gi[v] = G[0][v];
@@ -412,7 +430,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       nu3 = nu[2];
     } else if (role == 1) {
       float Jh;
-      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { w.Gi[v] = G[0][v]; w.Gj[v] = 0.f; }
       w.Li = make_float2(lt[0], nu[0]);
@@ -421,7 +439,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       sm.Li[ny * GIW + nx + 1] = w.Li;
     } else {
       float Jh;
-      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { w.Gj[v] = G[1][v]; w.Gi[v] = 0.f; }
       w.Lj = make_float2(lt[1], nu[1]);
@@ -429,6 +447,18 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, w.Gj);
       sm.Lj[(ny + 1) * TI + nx] = w.Lj;
     }
+  };
+
+  // k data of plane kk only (tile threads), nothing written to shared memory
+  auto node_pass_k = [&](int kk, float G3[5], float& lt3, float& nu3, float& Jn) {
+    if (role != 0) return;
+    float G[3][5], lt[3], nu[3];
+    node_v<3>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, pslot(kk - 1), pslot(kk), pslot(kk + 1), slot(kk), nx, ny, c, G,
+              lt, nu, Jn);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) G3[v] = G[2][v];
+    lt3 = lt[2];
+    nu3 = nu[2];
   };
 
   // face fluxes of plane kk on the low side of this thread's node: i face
@@ -523,7 +553,9 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   wait(2, 0, t0);
   convert(scr[1], t0);
   wait(3, 0, t0 + 1);
-  convert(scr[2], t0 + 1);
+  // plane t0+1: conserved record now; its primitive slot still holds plane
+  // t0-2, which the node pass of plane t0-1 reads
+  convert_parts(scr[2], t0 + 1, true, false);
   if (__syncthreads_or(!ok)) goto fail;
   issue_raw(t0 + 2, B_RAW, sm.raw, raw_parity(t0 + 2));
 
@@ -535,9 +567,11 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     // node pass of plane t0-1 (its k data only), of plane t0, the k face
     // t0 - 1/2, the i/j faces of plane t0 and the conversion of plane t0+2
     wait(B_MET, met_parity(t0 - 1), t0 - 1);
-    node_pass(t0 - 1, w, G3m, lt3m, nu3m, Jm);
+    node_pass_k(t0 - 1, G3m, lt3m, nu3m, Jm);
     if (__syncthreads_or(!ok)) goto fail;
     issue_met(t0);
+    convert_parts(scr[2], t0 + 1, false, true);  // scr[2] is overwritten by the node pass below
+    if (__syncthreads_or(!ok)) goto fail;
     wait(B_MET, met_parity(t0), t0);
     node_pass(t0, w, G3c, lt3c, nu3c, Jc);
     if (role == 0) {
@@ -628,12 +662,13 @@ fail:
   return false;
 }
 
-__global__ void __launch_bounds__(vr::NT, 1) k_stage_v(const __grid_constant__ StageCtx<float, float> X, const StageSel st) {
+__global__ void __launch_bounds__(vr::NT, vr::MINB)
+    k_stage_v(const __grid_constant__ StageCtx<float, float> X, const StageSel st) {
   extern __shared__ __align__(128) unsigned char smem[];
   item_v(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true);
 }
 
-__global__ void __launch_bounds__(vr::NT, 1)
+__global__ void __launch_bounds__(vr::NT, vr::MINB)
     k_stage_v_batch(const StageCtx<float, float>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
                     unsigned int* queue, const StageSel st) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -672,8 +707,8 @@ cudaError_t VR_FN(launch_stage_v_batch)(const void* ctx, const int4* items, int 
                                         const StageSel& st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  const int sms = device_sm_count();
-  const int ctas = nitems < sms ? nitems : sms;
+  const int slots = device_sm_count() * vr::MINB;
+  const int ctas = nitems < slots ? nitems : slots;
   k_stage_v_batch<<<ctas, vr::NT, vr::BYTES, s>>>((const StageCtx<float, float>*)ctx, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
