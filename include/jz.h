@@ -196,6 +196,48 @@ int jz_block_bytes(const jz_grid_desc* desc, const int o0[3], const int o1[3], s
 int jz_block_create(const jz_grid_desc* desc, const int o0[3], const int o1[3], void* dev_buf, size_t bytes,
                     void* stream, jz_grid** out);
 
+/* --- a block whose neighbours live on other ranks (Section 4.1: the
+ * partitioned domain, one partition per process; Section 4.3: the
+ * non-blocking exchange of two ghost layers of Q at every Runge-Kutta stage;
+ * Section 4.2, Fig. jazzy: where the exchanges sit in the stage sequence).
+ * The caller moves the face buffers between ranks (point-to-point sends, no
+ * collective) and combines the blocks' rates (a maximum over ranks).  One
+ * time step of a block, every call enqueued on the block's stream:
+ *   exchange of state copy 0 (pack, send / receive, unpack, per direction
+ *   i, j, k, so that edge and corner ghosts take values already exchanged);
+ *   jz_block_rate; the maximum of the rates over all blocks written back to
+ *   *dev_rate; jz_block_advance;
+ *   for stage l = 0..4: jz_block_stage(l), then (l < 4) the exchange of
+ *   state copy (1, 2, 1, 2)[l].
+ * State copies: 0 = Q0 (Q^n, Q^(5)), 1 = QA, 2 = QB.
+ *
+ * jz_halo_bytes: bytes of the buffer of one face normal to direction dir
+ *   (0 = i, 1 = j, 2 = k): 5 variables x 2 layers x the padded node counts
+ *   (n + 4) of the other two directions, in the state's type (FP64 for
+ *   JZ_P64, else FP32).
+ * jz_halo_pack: the two node layers just inside face (dir, side) (side 0:
+ *   nodes 0, 1; side 1: nodes n-2, n-1) of state copy `which`, over the
+ *   padded extents of the other directions, into buf (device, >=
+ *   jz_halo_bytes; layout [v][layer][b][a], a the first of the other two
+ *   directions in i, j, k order, fastest).
+ * jz_halo_unpack: buf into the two ghost layers behind the face (side 0:
+ *   nodes -2, -1; side 1: n, n+1); the neighbour packed its layers in the
+ *   same order, nearest-to-low first.
+ * jz_block_rate: enqueue this block's largest stable-step rate (Section 3
+ *   time step reading R12) into a device FP64 scalar and return its address
+ *   (valid while the block lives).
+ * jz_block_advance: enqueue dt = cfl / *rate, time += dt, step += 1.
+ * jz_block_stage: enqueue Runge-Kutta stage l (0..4) and the boundary pass
+ *   of its output copy (exchange ghosts are left to the caller).
+ * JZ_EINVAL for a face that is not an exchange face, a bad direction, side,
+ * copy or stage, a null pointer, or cfl <= 0. */
+int jz_halo_bytes(jz_grid* g, int dir, size_t* bytes);
+int jz_halo_pack(jz_grid* g, int which, int dir, int side, void* buf);
+int jz_halo_unpack(jz_grid* g, int which, int dir, int side, const void* buf);
+int jz_block_rate(jz_grid* g, double** dev_rate);
+int jz_block_advance(jz_grid* g, double cfl);
+int jz_block_stage(jz_grid* g, int stage);
+
 /* Set the flow parameters and enqueue the initial state (JZ_IC_JET: top-hat
  * profile plus noise drawn from SplitMix64(seed ^ (3 lin + m)); or air at
  * rest), then the boundary conditions.  Resets time and step to 0. */

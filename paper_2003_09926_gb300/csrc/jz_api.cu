@@ -740,6 +740,69 @@ int jz_set_stage_variant(jz_grid* g, int variant) {
   return build_maps(g->dev);  // the two kernels may stage different tiles
 }
 
+// --- a block of a grid partitioned over ranks ------------------------------
+
+static int halo_args(jz_grid* g, int which, int dir, int side) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (which < 0 || which > 2) return fail(JZ_EINVAL, "state copy %d is not 0 (Q0), 1 (QA) or 2 (QB)", which);
+  if (dir < 0 || dir > 2 || side < 0 || side > 1) return fail(JZ_EINVAL, "bad face (direction %d, side %d)", dir, side);
+  if (g->dev.L.bc[2 * dir + side] != BC_EXCHANGE)
+    return fail(JZ_EINVAL, "face (direction %d, side %d) is not an exchange face of this block", dir, side);
+  return JZ_OK;
+}
+
+static void* state_copy(GridDev& d, int which) { return which == 0 ? d.Q0 : (which == 1 ? d.QA : d.QB); }
+
+int jz_halo_bytes(jz_grid* g, int dir, size_t* bytes) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (dir < 0 || dir > 2 || !bytes) return fail(JZ_EINVAL, "bad direction %d or null output", dir);
+  const Layout& L = g->dev.L;
+  const int e1 = dir == 0 ? 1 : 0, e2 = dir == 2 ? 1 : 2;
+  *bytes = 10ULL * (size_t)(L.n[e1] + 2 * NG) * (size_t)(L.n[e2] + 2 * NG) * (g->dev.prec == JZ_P64 ? 8 : 4);
+  return JZ_OK;
+}
+
+int jz_halo_pack(jz_grid* g, int which, int dir, int side, void* buf) {
+  if (int rc = halo_args(g, which, dir, side)) return rc;
+  if (!buf) return fail(JZ_EINVAL, "null halo buffer");
+  const int first = side == 0 ? 0 : g->dev.L.n[dir] - 2;
+  JZ_CUDA(launch_halo(g->dev, state_copy(g->dev, which), buf, dir, first, true, g->stream));
+  return JZ_OK;
+}
+
+int jz_halo_unpack(jz_grid* g, int which, int dir, int side, const void* buf) {
+  if (int rc = halo_args(g, which, dir, side)) return rc;
+  if (!buf) return fail(JZ_EINVAL, "null halo buffer");
+  const int first = side == 0 ? -NG : g->dev.L.n[dir];
+  JZ_CUDA(launch_halo(g->dev, state_copy(g->dev, which), const_cast<void*>(buf), dir, first, false, g->stream));
+  return JZ_OK;
+}
+
+int jz_block_rate(jz_grid* g, double** dev_rate) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (!dev_rate) return fail(JZ_EINVAL, "null output");
+  JZ_CUDA(launch_rate(g->dev, g->stream));
+  *dev_rate = &g->dev.sc->rate;
+  return JZ_OK;
+}
+
+int jz_block_advance(jz_grid* g, double cfl) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(JZ_EINVAL, "cfl must be positive and finite (%g)", cfl);
+  JZ_CUDA(launch_advance_from_rate(g->dev, cfl, g->stream));
+  return JZ_OK;
+}
+
+int jz_block_stage(jz_grid* g, int stage) {
+  if (int rc = check_grid(g, true)) return rc;
+  if (stage < 0 || stage > 4) return fail(JZ_EINVAL, "stage %d is not 0..4", stage);
+  GridDev& d = g->dev;
+  const int src[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
+  JZ_CUDA(launch_stage(d, stage, src[stage], out[stage], g->stream));
+  JZ_CUDA(launch_bc(d, state_copy(d, out[stage]), g->stream));
+  return JZ_OK;
+}
+
 int jz_set_stall_test(jz_grid* g, int on) {
   if (int rc = check_grid(g, false)) return rc;
   if (on != 0 && on != 1) return fail(JZ_EINVAL, "stall test flag must be 0 or 1");

@@ -631,6 +631,36 @@ __global__ void k_exchange(const XEntry* __restrict__ xs, int which) {
   }
 }
 
+// Face halo of a block for a neighbour on another rank: the two node layers
+// [first, first + 1] along direction d over the padded extents of the other
+// two directions, as a dense buffer [v][l][b][a] (a fastest: direction e1,
+// then e2, in i, j, k order).  pack copies state -> buffer, unpack buffer ->
+// state.
+template <typename ST, bool PACK>
+__global__ void k_halo(Layout L, ST* __restrict__ Q, ST* __restrict__ buf, int d, int first) {
+  const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  const int ea = L.n[e1] + 2 * NG, eb = L.n[e2] + 2 * NG;
+  const long long per_var = 2LL * ea * eb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * per_var;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / per_var);
+    long long r = t - v * per_var;
+    const int a = (int)(r % ea) - NG;
+    r /= ea;
+    const int b = (int)(r % eb) - NG;
+    const int l = (int)(r / eb);
+    int idx[3];
+    idx[d] = first + l;
+    idx[e1] = a;
+    idx[e2] = b;
+    const long long o = v * L.npad + L.at(idx[0], idx[1], idx[2]);
+    if (PACK)
+      buf[t] = Q[o];
+    else
+      Q[o] = buf[t];
+  }
+}
+
 // axial inflow velocity of the jet profile at the x- face nodes (FP64, once per state_init)
 __global__ void k_inflow(Layout L, Coords C, FlowC F, double* __restrict__ inflow) {
   const int n = L.n[1] * L.n[2];
@@ -922,6 +952,21 @@ cudaError_t launch_pack(const GridDev& g, double* dense, cudaStream_t s) {
     k_pack<double><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const double*)g.Q0, nullptr, dense);
   else
     k_pack<float><<<grid_blocks(N, 256), 256, 0, s>>>(g.L, (const float*)g.Q0, g.Q0d, dense);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo(const GridDev& g, void* Q, void* buf, int d, int first, bool pack, cudaStream_t s) {
+  const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+  const long long N = 10LL * (g.L.n[e1] + 2 * NG) * (g.L.n[e2] + 2 * NG);
+  const int blocks = grid_blocks(N, 256);
+  if (g.prec == JZ_P64) {
+    if (pack) k_halo<double, true><<<blocks, 256, 0, s>>>(g.L, (double*)Q, (double*)buf, d, first);
+    else k_halo<double, false><<<blocks, 256, 0, s>>>(g.L, (double*)Q, (double*)buf, d, first);
+  } else {
+    if (pack) k_halo<float, true><<<blocks, 256, 0, s>>>(g.L, (float*)Q, (float*)buf, d, first);
+    else k_halo<float, false><<<blocks, 256, 0, s>>>(g.L, (float*)Q, (float*)buf, d, first);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

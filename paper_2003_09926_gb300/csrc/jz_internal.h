@@ -90,6 +90,13 @@ struct XEntry {
 };
 cudaError_t launch_exchange(int prec, const void* entries, int begin, int count, int blocks, int which,
                             cudaStream_t s);
+// two node layers [first, first + 1] along d (padded extents of the other
+// directions) of state Q to / from a dense buffer (pack: state -> buffer)
+cudaError_t launch_halo(const GridDev& g, void* Q, void* buf, int d, int first, bool pack, cudaStream_t s);
+// a block's stable-step rate into sc->rate (no time step taken), and the
+// time step from a rate already combined over the grid's blocks
+cudaError_t launch_rate(const GridDev& g, cudaStream_t s);
+cudaError_t launch_advance_from_rate(const GridDev& g, double cfl, cudaStream_t s);
 
 // jz_stats.cu: time statistics of the axial velocity
 cudaError_t launch_stats_sample(const GridDev& g, double* su, double* su2, cudaStream_t s);

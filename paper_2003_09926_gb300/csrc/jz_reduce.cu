@@ -161,8 +161,8 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
 template <typename ST, typename MT>
 __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, const ST* __restrict__ Q,
                                                           const MT* __restrict__ M, Scalars* sc, double* partial,
-                                                          double cfl) {
-  timestep_body<ST, MT>(L, F, Q, M, sc, partial, cfl);
+                                                          double cfl, bool finalize) {
+  timestep_body<ST, MT>(L, F, Q, M, sc, partial, cfl, finalize);
 }
 
 // batched: grid blockIdx.y of the table; gridDim.x blocks per grid
@@ -195,6 +195,15 @@ __global__ void k_rate_combine(const RateCtx* __restrict__ ctx, int n, double cf
     sc->time += dt;
     sc->step += 1;
   }
+}
+
+// one block of a grid partitioned over ranks: its rate has been combined with
+// the other blocks' (the largest) by the caller
+__global__ void k_advance_from_rate(Scalars* sc, double cfl) {
+  const double dt = cfl / sc->rate;
+  sc->dt = dt;
+  sc->time += dt;
+  sc->step += 1;
 }
 
 __global__ void k_fixed_dt(Scalars* sc, double dt) {
@@ -333,17 +342,42 @@ cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaS
   switch (g.prec) {
     case JZ_P64:
       k_timestep<double, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
-                                                                    (const double*)g.M, g.sc, g.partial, cfl);
+                                                                    (const double*)g.M, g.sc, g.partial, cfl, true);
       break;
     case JZ_P32_M64:
       k_timestep<float, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
-                                                                   (const double*)g.M, g.sc, g.partial, cfl);
+                                                                   (const double*)g.M, g.sc, g.partial, cfl, true);
       break;
     default:
       k_timestep<float, float><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
-                                                                  g.sc, g.partial, cfl);
+                                                                  g.sc, g.partial, cfl, true);
       break;
   }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rate(const GridDev& g, cudaStream_t s) {
+  switch (g.prec) {
+    case JZ_P64:
+      k_timestep<double, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
+                                                                    (const double*)g.M, g.sc, g.partial, 1.0, false);
+      break;
+    case JZ_P32_M64:
+      k_timestep<float, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
+                                                                   (const double*)g.M, g.sc, g.partial, 1.0, false);
+      break;
+    default:
+      k_timestep<float, float><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
+                                                                  g.sc, g.partial, 1.0, false);
+      break;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_from_rate(const GridDev& g, double cfl, cudaStream_t s) {
+  k_advance_from_rate<<<1, 1, 0, s>>>(g.sc, cfl);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -100,6 +100,12 @@ def lib() -> C.CDLL:
             "jz_set_tiling": ([G, C.c_int], C.c_int),
             "jz_set_stage_variant": ([G, C.c_int], C.c_int),
             "jz_set_stall_test": ([G, C.c_int], C.c_int),
+            "jz_halo_bytes": ([G, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+            "jz_halo_pack": ([G, C.c_int, C.c_int, C.c_int, VP], C.c_int),
+            "jz_halo_unpack": ([G, C.c_int, C.c_int, C.c_int, VP], C.c_int),
+            "jz_block_rate": ([G, C.POINTER(C.c_void_p)], C.c_int),
+            "jz_block_advance": ([G, C.c_double], C.c_int),
+            "jz_block_stage": ([G, C.c_int], C.c_int),
             "jz_set_tile_shape": ([G, C.c_int, C.c_int], C.c_int),
             "jz_fma_peak": ([C.c_int, C.POINTER(C.c_double), VP], C.c_int),
         }
@@ -280,6 +286,35 @@ def jz_set_tiling(h, kc: int) -> None:
 
 def jz_set_stage_variant(h, variant: int) -> None:
     _check(lib().jz_set_stage_variant(h, variant))
+
+
+def jz_halo_bytes(h, d: int) -> int:
+    n = C.c_size_t()
+    _check(lib().jz_halo_bytes(h, d, C.byref(n)))
+    return n.value
+
+
+def jz_halo_pack(h, which: int, d: int, side: int, dev_ptr: int) -> None:
+    _check(lib().jz_halo_pack(h, which, d, side, C.c_void_p(dev_ptr)))
+
+
+def jz_halo_unpack(h, which: int, d: int, side: int, dev_ptr: int) -> None:
+    _check(lib().jz_halo_unpack(h, which, d, side, C.c_void_p(dev_ptr)))
+
+
+def jz_block_rate(h) -> int:
+    """Enqueue the block's rate; returns the device address of its FP64 scalar."""
+    p = C.c_void_p()
+    _check(lib().jz_block_rate(h, C.byref(p)))
+    return p.value
+
+
+def jz_block_advance(h, cfl: float) -> None:
+    _check(lib().jz_block_advance(h, cfl))
+
+
+def jz_block_stage(h, stage: int) -> None:
+    _check(lib().jz_block_stage(h, stage))
 
 
 def jz_set_stall_test(h, on: bool) -> None:
