@@ -520,28 +520,35 @@ def fifo_extrapolation(trace, rate_mpt: float) -> dict:
 
 
 def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 256, base64_n: int = 4,
-                  pts_hi: float = 2e7, orders=("remaining",), fill: int = 4 * 10**6):
-    """Continuous batching on the serving trace: log-uniform 1e5..pts_hi
-    points per case (the configuration's 2e7 by default), 50..500 steps,
-    Poisson arrivals at 70% of the measured batched capacity, 150 GB HBM
-    budget, 10-step slices; against the same trace served one case at a
-    time in FP32, and in plain FP64 on its first cases with the full trace
-    extrapolated at the FP64 rate measured there."""
+                  pts_hi: float = 2e7, orders=(), fill: int = 4 * 10**6):
+    """Continuous serving of the trace: log-uniform 1e5..pts_hi points per
+    case (the configuration's 2e7 by default), 50..500 steps, Poisson
+    arrivals at 70% of the measured batched capacity, 150 GB HBM budget.
+    Headline: prioritised streams (at most 4 resident cases, the oldest on
+    the highest-priority stream, 20-step chunks); optionally the time-slice
+    server with batched launches in the given slice orders; against the
+    same trace served one case at a time in FP32, and in plain FP64 on its
+    first cases with the full trace extrapolated at the FP64 rate measured
+    there."""
     from paper_2003_09926_gb300 import serve
     cfg = W.config4(nreq=nreq, pts_hi=pts_hi)
     work = np.mean([interior_points(r["grid"]) * 5 * r["steps"] for r in cfg["requests"]])
     rate = 0.7 * capacity * 1e6 / work
     trace = serve.poisson_trace(cfg, rate)
     out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..{pts_hi:.0e} points, 50..500 steps, seed 4",
-           "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9, "slice_steps": 10}
+           "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9}
+    srv = serve.PriorityServer(150 * 10**9, max_running=4, chunk_steps=20, device=local)
+    out["fp32_continuous_priority_streams"] = dict(
+        serve.summarize(srv.run(trace)), max_running=4, chunk_steps=20, chunks=srv.chunks,
+        peak_resident_bytes=srv.peak_bytes,
+        policy="cases admitted in arrival order as memory and one of 4 slots free up; each advances with its own "
+               "graph-replayed steps, 20 at a time, on the stream of its arrival rank (oldest = highest priority), "
+               "so later cases run in the capacity the oldest leaves idle")
     for order in orders:
         srv = serve.Server(150 * 10**9, slice_steps=10, device=local, fill_points=fill, order=order)
         res = srv.run(trace)
-        key = "fp32_continuous_batching" if order == orders[0] else f"fp32_continuous_batching_{order}"
-        out[key] = dict(serve.summarize(res), fill_points=fill, order=order,
-                        policy=("least remaining work first" if order == "remaining" else "oldest first")
-                        + " until the selected cases hold fill_points points; a single case runs alone",
-                        peak_resident_bytes=srv.peak_bytes, slices=srv.slices)
+        out[f"fp32_time_slices_{order}"] = dict(serve.summarize(res), fill_points=fill, order=order, slice_steps=10,
+                                                peak_resident_bytes=srv.peak_bytes, slices=srv.slices)
     out["fp32_one_at_a_time"] = serve.summarize(serve.serve_one_at_a_time(trace, W.P32, device=local))
     first = serve.serve_one_at_a_time(trace[:base64_n], W.P64, device=local)
     busy = sum(r.finished - r.admitted for r in first)
@@ -607,8 +614,9 @@ def main(argv=None):
     ap.add_argument("--serving-quick", action="store_true",
                     help="serve a bounded 32-case trace of at most 2e6 points instead of the configuration's 256 "
                          "cases of 1e5..2e7 points (several minutes)")
-    ap.add_argument("--serving-orders", default="remaining",
-                    help="comma-separated slice orders to serve the trace with (remaining, arrival)")
+    ap.add_argument("--serving-orders", default="",
+                    help="also serve the trace with the time-slice server in these comma-separated slice orders "
+                         "(remaining, arrival, head)")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -773,7 +781,7 @@ def main(argv=None):
         line["batched"] = bench_batched(jz, torch, W, local, steps=max(10, args.steps // 5), steps64=2)
     if not args.no_serving:
         cap = line["batched"]["fp32_batched"]["value"] if "batched" in line else results[head]["value"]
-        orders = tuple(args.serving_orders.split(","))
+        orders = tuple(o for o in args.serving_orders.split(",") if o)
         line["serving"] = (bench_serving(jz, torch, W, local, cap, nreq=32, pts_hi=2e6, orders=orders)
                            if args.serving_quick else bench_serving(jz, torch, W, local, cap, orders=orders))
     if not args.no_cylinder:

@@ -180,6 +180,14 @@ int jz_grid_create(const jz_grid_desc* desc, void* dev_buf, size_t bytes, void* 
 /* Release the handle (and any captured graph).  Does not free dev_buf. */
 int jz_grid_destroy(jz_grid* g);
 
+/* Enqueue the grid's later work on `stream` (cudaStream_t as void*; NULL =
+ * legacy default stream), ordered after everything enqueued so far on its
+ * previous stream (an event recorded there, waited for on the new one).
+ * The library has no counterpart in the paper: a serving loop uses it to
+ * move a case between streams of different priority.  No host sync.
+ * Batches keep the stream they were created with. */
+int jz_set_stream(jz_grid* g, void* stream);
+
 /* --- blocks of a grid (the paper's domain decomposition, Section 4.2) -----
  * A block holds the nodes [o0[d], o1[d]] (inclusive, d = i, j, k) of the grid
  * `desc` describes, with its own two ghost layers: every jz_grid entry point

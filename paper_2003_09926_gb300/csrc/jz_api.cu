@@ -205,6 +205,7 @@ struct jz_grid {
   bool profiling = false;
   std::vector<EventPair> events;
   std::vector<cudaEvent_t> pool;
+  cudaEvent_t handoff = nullptr;  // orders a new stream after the old one (jz_set_stream)
 };
 
 struct jz_batch {
@@ -511,7 +512,19 @@ int jz_grid_destroy(jz_grid* g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   for (auto& p : g->events) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : g->pool) cudaEventDestroy(e);
+  if (g->handoff) cudaEventDestroy(g->handoff);
   delete g;
+  return JZ_OK;
+}
+
+int jz_set_stream(jz_grid* g, void* stream) {
+  if (int rc = check_grid(g, false)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (s == g->stream) return JZ_OK;
+  if (!g->handoff) JZ_CUDA(cudaEventCreateWithFlags(&g->handoff, cudaEventDisableTiming));
+  JZ_CUDA(cudaEventRecord(g->handoff, g->stream));
+  JZ_CUDA(cudaStreamWaitEvent(s, g->handoff, 0));
+  g->stream = s;
   return JZ_OK;
 }
 

@@ -100,6 +100,7 @@ def lib() -> C.CDLL:
             "jz_set_tiling": ([G, C.c_int], C.c_int),
             "jz_set_stage_variant": ([G, C.c_int], C.c_int),
             "jz_set_stall_test": ([G, C.c_int], C.c_int),
+            "jz_set_stream": ([G, VP], C.c_int),
             "jz_halo_bytes": ([G, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
             "jz_halo_pack": ([G, C.c_int, C.c_int, C.c_int, VP], C.c_int),
             "jz_halo_unpack": ([G, C.c_int, C.c_int, C.c_int, VP], C.c_int),
@@ -396,6 +397,11 @@ class Grid:
         if out is None:
             out = np.empty(self.shape)
         return jz_state_download(self.h, out)
+
+    def set_stream(self, stream) -> None:
+        """Enqueue later work on `stream` (a torch.cuda.Stream), after the work so far."""
+        _check(lib().jz_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+        self.stream = stream
 
     def metrics(self) -> np.ndarray:
         """[10][nk][nj][ni] FP64: S^k_m at 3k+m, J at 9."""

@@ -6,9 +6,14 @@ fits an HBM budget; admitted cases stay resident on the device and advance
 together in time slices, each slice one batched launch sequence
 (``jz_batch_nsteps``) over the resident grids it selects: all of them, or
 (``fill_points``) cases in the order of ``order`` until they hold enough
-points to fill the GPU -- "arrival" (oldest first) or "remaining" (least
+points to fill the GPU -- "arrival" (oldest first), "remaining" (least
 remaining work, points x steps left, first: the smallest cases finish
-first and share the GPU only where one case alone cannot fill it).
+first) or "head" (the oldest case, then the least remaining work: the
+oldest case advances in arrival order as it would alone, and only the
+smallest cases share the GPU with it, where it cannot fill it alone).
+Up to two slices are in flight on the device; the host waits for a slice
+only when a case finishes in it (to read its result) and before it frees
+device memory.
 Finished cases are retired at slice boundaries -- their diagnostics (and
 optionally their state) are read back and their memory returned -- so cases
 that arrive while others run are admitted as soon as memory frees up and
@@ -80,19 +85,25 @@ def remaining_work(c: dict) -> int:
 
 def select_cases(resident: list[dict], fill_points: int | None, order: str = "arrival") -> list[dict]:
     """The resident cases one slice advances: every case when fill_points is
-    None, else cases in the given order -- "arrival" (arrival, then id) or
-    "remaining" (least remaining work, then arrival and id) -- until their
-    updated points reach fill_points."""
+    None, else cases in the given order -- "arrival" (arrival, then id),
+    "remaining" (least remaining work, then arrival and id) or "head" (the
+    oldest, then least remaining work) -- until their updated points reach
+    fill_points."""
     if fill_points is None:
         return list(resident)
+    oldest = lambda c: (c["req"].arrival, c["req"].rid)  # noqa: E731
+    smallest = lambda c: (remaining_work(c), c["req"].arrival, c["req"].rid)  # noqa: E731
     if order == "remaining":
-        key = lambda c: (remaining_work(c), c["req"].arrival, c["req"].rid)  # noqa: E731
+        ranked = sorted(resident, key=smallest)
     elif order == "arrival":
-        key = lambda c: (c["req"].arrival, c["req"].rid)  # noqa: E731
+        ranked = sorted(resident, key=oldest)
+    elif order == "head":
+        head = min(resident, key=oldest)
+        ranked = [head] + sorted((c for c in resident if c is not head), key=smallest)
     else:
         raise ValueError(f"unknown order {order!r}")
     chosen, pts = [], 0
-    for c in sorted(resident, key=key):
+    for c in ranked:
         chosen.append(c)
         pts += updated_points(c["req"].grid)
         if pts >= fill_points:
@@ -112,14 +123,36 @@ class CudaBackend:
     def grid_bytes(self, desc: dict) -> int:
         return jz.jz_grid_bytes(desc)
 
-    def grid(self, desc: dict, flow: dict, seed: int, kc: int | None):
-        g = jz.Grid(desc, stream=self.stream, device=self.device).init(flow, seed)
+    def grid(self, desc: dict, flow: dict, seed: int, kc: int | None, stream=None):
+        g = jz.Grid(desc, stream=stream if stream is not None else self.stream, device=self.device).init(flow, seed)
         if kc is not None:
             jz.jz_set_tiling(g.h, int(kc))
         return g
 
+    def priority_streams(self, n: int) -> list:
+        """n streams, highest priority first (levels beyond the device's range
+        share its lowest level)."""
+        import torch
+        least, greatest = torch.cuda.Stream.priority_range()
+        step = -1 if greatest < least else 1
+        levels = list(range(greatest, least - step, -step))  # highest first
+        return [torch.cuda.Stream(device=self.device, priority=levels[min(i, len(levels) - 1)]) for i in range(n)]
+
     def batch(self, grids):
         return jz.Batch(grids, stream=self.stream)
+
+    def mark(self, stream=None):
+        """An event recorded on the stream after the work enqueued so far."""
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(stream if stream is not None else self.stream)
+        return ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def wait(self, ev) -> None:
+        ev.synchronize()
 
     def synchronize(self):
         self.stream.synchronize()
@@ -136,7 +169,7 @@ class Server:
         self.keep_state = keep_state
         self.kc_for = kc_for  # optional callable grid-desc -> k-chunk length (autotuner)
         self.fill_points = fill_points
-        if order not in ("arrival", "remaining"):
+        if order not in ("arrival", "remaining", "head"):
             raise ValueError(f"unknown order {order!r}")
         self.order = order
         self.backend = backend if backend is not None else CudaBackend(device)
@@ -173,6 +206,12 @@ class Server:
             for key in [k for k in batches if not set(k) <= live]:
                 batches.pop(key).close()
 
+        inflight: list = []  # events of slices still running (at most two)
+
+        def drain() -> None:
+            be.synchronize()
+            inflight.clear()
+
         while pending or resident:
             # cancellations take effect here, between slices
             gone = cancelled_now()
@@ -182,6 +221,7 @@ class Server:
                     results[r.rid] = Result(r.rid, "cancelled", r.arrival, finished=now())
                 hit = [c for c in resident if c["req"].rid in gone]
                 if hit:
+                    drain()  # no kernel of theirs may still run when their memory is freed
                     resident = [c for c in resident if c["req"].rid not in gone]
                     drop_batches({c["req"].rid for c in resident})
                     for c in hit:
@@ -221,13 +261,17 @@ class Server:
                 if key not in batches:
                     batches[key] = be.batch([c["grid"] for c in chosen])
                 batches[key].nsteps(n, self.cfl)
-            be.synchronize()
             self.slices += 1
-            advanced = {id(c) for c in chosen}
+            for c in chosen:
+                c["left"] -= n
+            if any(c["left"] <= 0 for c in chosen):
+                drain()  # a case finished in this slice: its result is read now
+            else:
+                inflight.append(be.mark())
+                if len(inflight) > 1:
+                    be.wait(inflight.pop(0))
             still = []
             for c in resident:
-                if id(c) in advanced:
-                    c["left"] -= n
                 if c["left"] > 0:
                     still.append(c)
                     continue
@@ -242,8 +286,125 @@ class Server:
             if len(still) != len(resident):
                 drop_batches({c["req"].rid for c in still})
                 resident = still
+        drain()
         for b in batches.values():
             b.close()
+        return [results[k] for k in sorted(results)]
+
+
+class PriorityServer:
+    """Continuous serving on prioritised CUDA streams.
+
+    Cases are admitted in arrival order while their device footprint fits
+    the budget and fewer than ``max_running`` are resident.  Every resident
+    case advances with its own graph-replayed steps, ``chunk_steps`` at a
+    time, on the stream of its rank in arrival order: the oldest on the
+    highest-priority stream.  At every chunk boundary the ranks are renewed
+    (``jz_set_stream`` moves a case, ordered after its earlier work).  The
+    device's block scheduler serves higher-priority streams first, so the
+    oldest case proceeds about as it would alone -- first come, first
+    served for the long cases -- while later cases run in the capacity it
+    leaves idle (the partial last wave of each of its kernels and the gaps
+    between them) instead of waiting behind it.  Cases that arrive while
+    others run are admitted as slots and memory free up and their work
+    overlaps on the device; each case's arithmetic is its own, so its result
+    is the one it reaches alone.  Cancellation as in ``Server``.
+    Latency = completion - arrival (host clock; completion is polled)."""
+
+    def __init__(self, budget_bytes: int, max_running: int = 4, chunk_steps: int = 20, cfl: float = 0.5,
+                 device: int = 0, keep_state: bool = False, kc_for=None, backend=None):
+        self.budget = int(budget_bytes)
+        self.max_running = int(max_running)
+        self.chunk_steps = int(chunk_steps)
+        self.cfl = float(cfl)
+        self.keep_state = keep_state
+        self.kc_for = kc_for
+        self.backend = backend if backend is not None else CudaBackend(device)
+        self.peak_bytes = 0
+        self.chunks = 0
+        self._cancel_lock = threading.Lock()
+        self._cancelled: set[int] = set()
+
+    def cancel(self, rid: int) -> None:
+        with self._cancel_lock:
+            self._cancelled.add(int(rid))
+
+    def run(self, requests: list[Request]) -> list[Result]:
+        be = self.backend
+        streams = be.priority_streams(self.max_running)
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        results: dict[int, Result] = {}
+        resident: list[dict] = []  # in arrival order = priority order
+        used = 0
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+
+        def cancelled_now() -> set:
+            t = now()
+            with self._cancel_lock:
+                out = set(self._cancelled)
+            return out | {r.rid for r in requests if r.cancel_at is not None and r.cancel_at <= t}
+
+        while pending or resident:
+            gone = cancelled_now()
+            if gone:
+                for r in [r for r in pending if r.rid in gone]:
+                    pending.remove(r)
+                    results[r.rid] = Result(r.rid, "cancelled", r.arrival, finished=now())
+                for c in [c for c in resident if c["req"].rid in gone]:
+                    for ev in c["inflight"]:
+                        be.wait(ev)  # none of its kernels may run when its memory is freed
+                    resident.remove(c)
+                    res = results[c["req"].rid]
+                    res.status, res.finished = "cancelled", now()
+                    c["grid"].close()
+                    used -= c["bytes"]
+            while pending and pending[0].arrival <= now() and len(resident) < self.max_running:
+                r = pending[0]
+                need = be.grid_bytes(r.grid)
+                if need > self.budget:
+                    pending.pop(0)
+                    results[r.rid] = Result(r.rid, f"rejected: needs {need} bytes, budget {self.budget}", r.arrival)
+                    continue
+                if used + need > self.budget:
+                    break
+                pending.pop(0)
+                st = streams[len(resident)]
+                g = be.grid(r.grid, r.flow, r.seed, None if self.kc_for is None else self.kc_for(r.grid), stream=st)
+                used += need
+                self.peak_bytes = max(self.peak_bytes, used)
+                resident.append(dict(req=r, grid=g, left=r.steps, bytes=need, stream=st, inflight=[]))
+                results[r.rid] = Result(r.rid, "running", r.arrival, admitted=now(), points=updated_points(r.grid),
+                                        steps=r.steps)
+            progressed = False
+            for rank, c in enumerate(resident):
+                while c["inflight"] and be.done(c["inflight"][0]):
+                    c["inflight"].pop(0)
+                    progressed = True
+                if c["left"] > 0 and len(c["inflight"]) < 2:
+                    if c["stream"] is not streams[rank]:
+                        c["grid"].set_stream(streams[rank])
+                        c["stream"] = streams[rank]
+                    n = min(self.chunk_steps, c["left"])
+                    c["grid"].nsteps(n, cfl=self.cfl)
+                    c["left"] -= n
+                    c["inflight"].append(be.mark(c["stream"]))
+                    self.chunks += 1
+                    progressed = True
+            for c in [c for c in resident if c["left"] <= 0 and not c["inflight"]]:
+                res = results[c["req"].rid]
+                res.diag = c["grid"].diagnostics(allow_nonfinite=True)
+                if self.keep_state:
+                    res.state = c["grid"].download()
+                res.finished = now()
+                res.status = "done"
+                c["grid"].close()
+                used -= c["bytes"]
+                resident.remove(c)
+                progressed = True
+            if not progressed:
+                nxt = pending[0].arrival - now() if pending and not resident else 0.0
+                time.sleep(min(0.01, max(nxt, 0.0002)))
         return [results[k] for k in sorted(results)]
 
 

@@ -85,3 +85,21 @@ def test_served_p64_cases_match_the_oracle(mods):
         ref = o.inner(Q)
         err = max(np.abs(r.state[v] - ref[v]).max() / np.abs(ref[v]).max() for v in range(5))
         assert err <= 1e-10, (q.rid, err)
+
+
+def test_priority_server_results_same_alone_and_in_the_mix(mods):
+    """Prioritised streams: cases overlapping on the device (the oldest on
+    the highest-priority stream, moved up as older cases finish) each end
+    bitwise in the state they reach alone."""
+    jz, serve = mods
+    reqs = _trace(serve)
+    sizes = sorted(jz.jz_grid_bytes(r.grid) for r in reqs)
+    srv = serve.PriorityServer(sizes[-1] + sizes[-2] + sizes[-3], max_running=3, chunk_steps=4, keep_state=True)
+    res = srv.run(reqs)
+    assert all(r.status == "done" for r in res) and srv.chunks >= sum((q.steps + 3) // 4 for q in reqs)
+    for r, q in zip(res, reqs):
+        alone = jz.Grid(q.grid).init(q.flow, q.seed)
+        alone.nsteps(q.steps, cfl=0.5)
+        np.testing.assert_array_equal(r.state, alone.download())
+        assert r.diag["step"] == q.steps
+        alone.close()

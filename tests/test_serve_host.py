@@ -32,6 +32,10 @@ class FakeGrid:
         self.closed = True
         self.log.append(("close", self.seed))
 
+    def set_stream(self, stream):
+        self.log.append(("stream", self.seed, stream))
+        self.stream = stream
+
 
 class FakeBatch:
     def __init__(self, grids):
@@ -56,15 +60,30 @@ class FakeBackend:
     def grid_bytes(self, desc):
         return desc["ni"] * desc["nj"] * desc["nk"]
 
-    def grid(self, desc, flow, seed, kc):
+    def grid(self, desc, flow, seed, kc, stream=None):
         g = FakeGrid(self.log, desc, seed)
+        g.stream = stream
         self.grids[seed] = g
         return g
+
+    def priority_streams(self, n):
+        return [f"s{i}" for i in range(n)]
+
+    def done(self, ev):
+        return True
 
     def batch(self, grids):
         return FakeBatch(grids)
 
     def synchronize(self):
+        if self.slice_delay:
+            time.sleep(self.slice_delay)
+        self.log.append(("sync", None))
+
+    def mark(self, stream=None):
+        return object()
+
+    def wait(self, ev):
         if self.slice_delay:
             time.sleep(self.slice_delay)
 
@@ -126,6 +145,31 @@ def test_least_remaining_work_first():
     assert fin["arrival"][0] < fin["arrival"][1]
 
 
+def test_head_order_keeps_the_oldest_case_moving():
+    """'head': the oldest case is always in the slice; the fill comes from
+    the least remaining work."""
+    mk = lambda rid, n, left, arr: {"req": _req(rid, n, 100, arr), "left": left}  # noqa: E731
+    res = [mk(0, 20, 50, 0.0), mk(1, 10, 50, 1.0), mk(2, 30, 1, 2.0)]
+    assert [c["req"].rid for c in serve.select_cases(res, 6000, "head")] == [0, 2]
+    assert [c["req"].rid for c in serve.select_cases(res, 5000, "head")] == [0]
+    reqs = [_req(0, 20, 60), _req(1, 10, 10, arrival=0.0)]
+    be = FakeBackend()
+    out = serve.Server(10 ** 6, slice_steps=5, backend=be, fill_points=1, order="head").run(reqs)
+    assert [r.diag["step"] for r in out] == [60, 10]
+    assert out[0].finished < out[1].finished  # fill 1: the oldest runs alone, first
+
+
+def test_results_wait_for_their_slice():
+    """Slices are pipelined, but a case's result is read only after the
+    device has finished it (a synchronisation precedes every retirement)."""
+    be = FakeBackend()
+    reqs = [_req(0, 10, 30), _req(1, 12, 45)]
+    serve.Server(10 ** 6, slice_steps=10, backend=be, fill_points=10 ** 9).run(reqs)
+    for seed in (0, 1):
+        i = be.log.index(("close", seed))
+        assert ("sync", None) in be.log[:i]
+
+
 def test_select_cases_orders():
     mk = lambda rid, n, left, arr: {"req": _req(rid, n, 100, arr), "left": left}  # noqa: E731
     res = [mk(0, 20, 50, 0.0), mk(1, 10, 50, 1.0), mk(2, 30, 1, 2.0)]
@@ -136,3 +180,30 @@ def test_select_cases_orders():
     assert len(serve.select_cases(res, None)) == 3
     with pytest.raises(ValueError):
         serve.select_cases(res, 10, "random")
+
+
+def test_priority_server_ranks_streams_by_arrival():
+    """The oldest resident case always holds the highest-priority stream;
+    when it finishes, the next one moves up (at a chunk boundary)."""
+    be = FakeBackend()
+    reqs = [_req(0, 10, 40), _req(1, 10, 100), _req(2, 10, 60)]
+    srv = serve.PriorityServer(10 ** 6, max_running=3, chunk_steps=10, backend=be)
+    res = srv.run(reqs)
+    assert all(r.status == "done" for r in res) and [r.diag["step"] for r in res] == [40, 100, 60]
+    assert be.grids[0].stream == "s0"
+    moves = [e for e in be.log if e[0] == "stream"]
+    # case 1 moves to s0 after case 0 retires; case 2 to s1, then s0 after case 1... or retires first
+    assert ("stream", 1, "s0") in moves and ("stream", 2, "s1") in moves
+    assert be.log.index(("close", 0)) < be.log.index(("stream", 1, "s0"))
+    assert srv.chunks == 4 + 10 + 6
+
+
+def test_priority_server_budget_slots_and_cancel():
+    be = FakeBackend(slice_delay=0.0)
+    reqs = [_req(0, 10, 10 ** 5, cancel_at=0.02), _req(1, 10, 30), _req(2, 10, 20, arrival=0.01)]
+    srv = serve.PriorityServer(1000, max_running=4, chunk_steps=5, backend=be)  # memory for one case
+    res = srv.run(reqs)
+    assert res[0].status == "cancelled" and be.grids[0].closed
+    assert res[1].status == "done" and res[2].status == "done"
+    assert srv.peak_bytes == 1000
+    assert be.log.index(("close", 0)) < be.log.index(("create", 1)) < be.log.index(("create", 2))
