@@ -135,9 +135,11 @@ def measured_hbm_peak():
 
 
 # stage kernel source files and names per precision (0 P64, 1 P32_M64, 2 P32)
-STAGE_SOURCES = {2: ("jz_stage_v.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh"),
-                 1: ("jz_stage.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh"),
-                 0: ("jz_stage.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh")}
+# sources whose change invalidates a recorded DRAM traffic figure: the
+# kernel and its headers, and jz_api.cu (TMA tensor maps, default tile shape)
+STAGE_SOURCES = {2: ("jz_stage_v.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh", "jz_api.cu"),
+                 1: ("jz_stage.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh", "jz_api.cu"),
+                 0: ("jz_stage.cu", "jz_stage_common.cuh", "jz_fastmath.cuh", "jz_common.cuh", "jz_api.cu")}
 STAGE_KERNELS = {2: "k_stage_v (fused RK stage, vector node records)",
                  1: "k_stage<float,double,32,16> (fused RK stage)",
                  0: "k_stage<double,double,16,16> (fused RK stage)"}
