@@ -411,9 +411,10 @@ int jz_set_tiling(jz_grid* g, int kc);
  * for other variants.  A batch uses its first grid's variant. */
 int jz_set_stage_variant(jz_grid* g, int variant);
 
-/* Test of the bounded waits (SURVEY failure detection; the paper has no
- * counterpart).  on = 1: every TMA copy that the grid's stage kernels issue
- * expects 16 bytes more than it delivers, so no staging wait can complete,
+/* Test of the bounded waits: failure detection exercised without a GPU
+ * fault (the paper has no counterpart).  on = 1: every TMA copy that the
+ * grid's stage kernels issue expects 16 bytes more than it delivers, so no
+ * staging wait can complete,
  * and the waits give up after 2^16 SM cycles instead of about a second.
  * Each stage kernel then takes its timeout path: it records the failure in
  * the grid's sticky error flag, completes the missing bytes itself, waits
