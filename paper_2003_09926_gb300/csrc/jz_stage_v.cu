@@ -60,20 +60,26 @@ static_assert(NT % 32 == 0, "whole warps");
 constexpr int NCH = 3 * (NJH + NIH);            // plane elements converted by the halo threads
 constexpr int RW = TI + 4, RH = TJ + 4, PL = RW * RH;  // staged plane: tile + two-node halo (36 x 20)
 constexpr int MH = TJ + 2, MPL = RW * MH;        // metric box: rows -1 .. TJ, 36 columns
+// Warp layout of the tile threads.  A warp holds 32 nodes: a full row of a
+// 32-wide tile, or two rows of a 16-wide tile.  In the 16 x 16 build the two
+// rows of a warp are r and r + 4 (warps 0-3: rows 0-3 and 4-7, warps 4-7:
+// rows 8-11 and 12-15), and every per-row buffer has a row stride of 20
+// words, so the two half-warps of a scalar shared-memory access sit 80 = 16
+// (mod 32) banks apart and never conflict.
+constexpr bool ROWS4 = TI == 16 && TJ == 16;
 // ring records: rows padded to 37 so that the column-wise accesses of the
-// i-halo warp fall on distinct banks
-constexpr int RR = RW + 1, RPL = RR * RH;
+// i-halo warp fall on distinct banks (unpadded rows of 20 in the 16 x 16
+// build, for the warp layout above)
+constexpr int RR = ROWS4 ? RW : RW + 1, RPL = RR * RH;
 // ring depths (planes): conserved records 4 (the k face t + 1/2 reads
 // planes t-1 .. t+2), primitive records 3 (the node pass of plane t reads
 // planes t-1 .. t+1)
 constexpr int NSQ = 4, NSP = 3;
 // node buffers: columns -1..TI / rows -1..TJ; face buffers: i faces 0..TI /
-// j faces 0..TJ.  The i-direction rows are padded by one (distinct banks for
-// the i-halo warp's column accesses) except in the two-CTA build, which
-// needs the bytes.
-constexpr int IPAD = MINB > 1 ? 0 : 1;
-constexpr int GIW = TI + 2 + IPAD, GJH = TJ + 2;
-constexpr int HIW = TI + 2 + IPAD, HJH = TJ + 1;
+// j faces 0..TJ.  The i-direction rows are padded (distinct banks for the
+// i-halo warp's column accesses; a stride of 20 in the 16 x 16 build).
+constexpr int GIW = ROWS4 ? TI + 4 : TI + 3, GJH = TJ + 2;
+constexpr int HIW = ROWS4 ? TI + 4 : TI + 3, HJH = TJ + 1;
 constexpr size_t al(size_t x) { return (x + 127) / 128 * 128; }
 constexpr size_t RAW_B = al(4 * 5 * PL);
 constexpr size_t QV_B = al(16 * NSQ * RPL), QE_B = al(4 * NSQ * RPL);
@@ -82,10 +88,13 @@ constexpr size_t MET_B = al(4 * 10 * MPL);
 constexpr int UPL = RW * TJ;                     // Q^(0) box: tile rows, 36 columns
 constexpr size_t Q0_B = al(4 * 5 * UPL);
 constexpr size_t GI4_B = al(16 * TJ * GIW), GI1_B = al(4 * TJ * GIW);
-constexpr size_t GJ4_B = al(16 * GJH * TI), GJ1_B = al(4 * GJH * TI);
+// the scalar part of the j-direction records: rows of 20 in the 16 x 16 build
+// (the float4 / float2 parts are conflict-free at any row stride)
+constexpr int JS1 = ROWS4 ? TI + 4 : TI;
+constexpr size_t GJ4_B = al(16 * GJH * TI), GJ1_B = al(4 * GJH * JS1);
 constexpr size_t LI_B = al(8 * TJ * GIW), LJ_B = al(8 * GJH * TI);
 constexpr size_t HI4_B = al(16 * TJ * HIW), HI1_B = al(4 * TJ * HIW);
-constexpr size_t HJ4_B = al(16 * HJH * TI), HJ1_B = al(4 * HJH * TI);
+constexpr size_t HJ4_B = al(16 * HJH * TI), HJ1_B = al(4 * HJH * JS1);
 constexpr size_t O_RAW = 0;
 constexpr size_t O_QV = O_RAW + RAW_B;
 constexpr size_t O_QE = O_QV + QV_B;
@@ -128,6 +137,16 @@ __device__ __forceinline__ void ld5(const float4* v4, const float* v1, int i, fl
 __device__ __forceinline__ void st5(float4* v4, float* v1, int i, const float q[5]) {
   v4[i] = make_float4(q[0], q[1], q[2], q[3]);
   v1[i] = q[4];
+}
+// a record whose two parts have different row strides: row y, column x
+__device__ __forceinline__ void ld5j(const float4* v4, const float* v1, int y, int x, float q[5]) {
+  const float4 a = v4[y * vr::TI + x];
+  q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+  q[4] = v1[y * vr::JS1 + x];
+}
+__device__ __forceinline__ void st5j(float4* v4, float* v1, int y, int x, const float q[5]) {
+  v4[y * vr::TI + x] = make_float4(q[0], q[1], q[2], q[3]);
+  v1[y * vr::JS1 + x] = q[4];
 }
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -316,9 +335,29 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
 
   // node role: tile node, j-halo node (rows -1, TJ) or i-halo node (columns -1, TI)
   int nx, ny, role;
-  if (tid < NTILE) { role = 0; nx = tid % TI; ny = tid / TI; }
+  if (tid < NTILE) {
+    role = 0;
+    if (ROWS4) {  // warp w: rows (w & 3) + 8 (w >> 2) and 4 below it
+      const int w = tid >> 5, l = tid & 31;
+      nx = l & 15;
+      ny = (w & 3) + 8 * (w >> 2) + 4 * (l >> 4);
+    } else {
+      nx = tid % TI;
+      ny = tid / TI;
+    }
+  }
   else if (tid < NTILE + NJH) { role = 2; const int h = tid - NTILE; nx = h % TI; ny = (h / TI) ? TJ : -1; }
-  else { role = 1; const int h = tid - NTILE - NJH; ny = h % TJ; nx = (h / TJ) ? TI : -1; }
+  else {
+    role = 1;
+    const int h = tid - NTILE - NJH;
+    if (ROWS4) {  // both halo columns of four rows per quarter-warp: 2-way, not 4-way, bank conflicts
+      ny = h >> 1;
+      nx = (h & 1) ? TI : -1;
+    } else {
+      ny = h % TJ;
+      nx = (h / TJ) ? TI : -1;
+    }
+  }
   const int gi = i0 + nx, gj = j0 + ny;
   const bool own = role == 0 && gi >= L.lo[0] && gi <= L.hi[0] && gj >= L.lo[1] && gj <= L.hi[1];
 
@@ -393,7 +432,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       const float ri = Fn<float>::rcp(q0);
       const float u = q1 * ri, v = q2 * ri, w = q3 * ri;
       const float pr = c.gm1 * (q4 - 0.5f * q0 * (u * u + v * v + w * w));
-      const int r = e + e / RW;  // padded ring row
+      const int r = e + (RR - RW) * (e / RW);  // ring row (padded when RR > RW)
       if (CQ) {
         qv[r] = make_float4(q0, q1, q2, q3);
         qe[r] = q4;
@@ -423,7 +462,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       w.Li = make_float2(lt[0], nu[0]);
       w.Lj = make_float2(lt[1], nu[1]);
       st5(sm.Gi4, sm.Gi1, ny * GIW + nx + 1, w.Gi);
-      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, w.Gj);
+      st5j(sm.Gj4, sm.Gj1, ny + 1, nx, w.Gj);
       sm.Li[ny * GIW + nx + 1] = w.Li;
       sm.Lj[(ny + 1) * TI + nx] = w.Lj;
       lt3 = lt[2];
@@ -444,7 +483,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       for (int v = 0; v < 5; ++v) { w.Gj[v] = G[1][v]; w.Gi[v] = 0.f; }
       w.Lj = make_float2(lt[1], nu[1]);
       w.Li = make_float2(0.f, 0.f);
-      st5(sm.Gj4, sm.Gj1, (ny + 1) * TI + nx, w.Gj);
+      st5j(sm.Gj4, sm.Gj1, ny + 1, nx, w.Gj);
       sm.Lj[(ny + 1) * TI + nx] = w.Lj;
     }
   };
@@ -483,12 +522,12 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     }
     if (do_j) {
       float Ga[5], q0[5], q1[5], q3[5];
-      ld5(sm.Gj4, sm.Gj1, ny * TI + nx, Ga);
+      ld5j(sm.Gj4, sm.Gj1, ny, nx, Ga);
       ld5(qv, qe, oo - 2 * RR, q0);
       ld5(qv, qe, oo - RR, q1);
       ld5(qv, qe, oo + RR, q3);
       face_v(c, sm.Lj[ny * TI + nx], w.Lj, Ga, w.Gj, q0, q1, qo, q3, hj);
-      st5(sm.Hj4, sm.Hj1, ny * TI + nx, hj);
+      st5j(sm.Hj4, sm.Hj1, ny, nx, hj);
     }
   };
 
@@ -499,8 +538,8 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     float a[5], b[5], d[5], e[5];
     ld5(sm.Hi4, sm.Hi1, ny * HIW + nx + 1, a);
     ld5(sm.Hi4, sm.Hi1, ny * HIW + nx, d);
-    ld5(sm.Hj4, sm.Hj1, (ny + 1) * TI + nx, b);
-    ld5(sm.Hj4, sm.Hj1, ny * TI + nx, e);
+    ld5j(sm.Hj4, sm.Hj1, ny + 1, nx, b);
+    ld5j(sm.Hj4, sm.Hj1, ny, nx, e);
 #pragma unroll
     for (int v = 0; v < 5; ++v) R[v] = (a[v] - d[v]) + (b[v] - e[v]);
   };
