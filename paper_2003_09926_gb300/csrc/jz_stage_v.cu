@@ -40,6 +40,11 @@
 #define VR_TI 32
 #define VR_TJ 16
 #endif
+// face fluxes, node gradients and contravariant viscous fluxes on packed
+// FP32x2 component pairs
+#ifndef VR_PACKED_FACES
+#define VR_PACKED_FACES 1
+#endif
 #define VR_CAT3(a, b, c) a##_##b##x##c
 #define VR_CAT(a, b, c) VR_CAT3(a, b, c)
 #define VR_FN(name) VR_CAT(name, VR_TI, VR_TJ)
@@ -190,15 +195,38 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
     // Cartesian gradients of u, v, w, T: J/2 sum_k S^k_m (phi_+ - phi_-)
     const float4 a0 = pc[o + 1], b0 = pc[o - 1], a1 = pc[o + RR], b1 = pc[o - RR];
     const float4 a2 = PV[sP + o], b2 = PV[sM + o];
+    const float hJ = 0.5f * Jn;
+    float g[4][3];
+#if VR_PACKED_FACES
+    {  // the same sums on the variable pairs (u, v) and (w, T), packed FP32x2
+      const float2 m1 = make_float2(-1.f, -1.f), h2 = make_float2(hJ, hJ);
+      const float2 d0[2] = {__ffma2_rn(make_float2(b0.x, b0.y), m1, make_float2(a0.x, a0.y)),
+                            __ffma2_rn(make_float2(b0.z, b0.w), m1, make_float2(a0.z, a0.w))};
+      const float2 d1[2] = {__ffma2_rn(make_float2(b1.x, b1.y), m1, make_float2(a1.x, a1.y)),
+                            __ffma2_rn(make_float2(b1.z, b1.w), m1, make_float2(a1.z, a1.w))};
+      const float2 d2[2] = {__ffma2_rn(make_float2(b2.x, b2.y), m1, make_float2(a2.x, a2.y)),
+                            __ffma2_rn(make_float2(b2.z, b2.w), m1, make_float2(a2.z, a2.w))};
+#pragma unroll
+      for (int pq = 0; pq < 2; ++pq)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          float2 t = __fmul2_rn(make_float2(S[m], S[m]), d0[pq]);
+          t = __ffma2_rn(make_float2(S[3 + m], S[3 + m]), d1[pq], t);
+          t = __ffma2_rn(make_float2(S[6 + m], S[6 + m]), d2[pq], t);
+          t = __fmul2_rn(h2, t);
+          g[2 * pq][m] = t.x;
+          g[2 * pq + 1][m] = t.y;
+        }
+    }
+#else
     const float d0[4] = {a0.x - b0.x, a0.y - b0.y, a0.z - b0.z, a0.w - b0.w};
     const float d1[4] = {a1.x - b1.x, a1.y - b1.y, a1.z - b1.z, a1.w - b1.w};
     const float d2[4] = {a2.x - b2.x, a2.y - b2.y, a2.z - b2.z, a2.w - b2.w};
-    const float hJ = 0.5f * Jn;
-    float g[4][3];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int m = 0; m < 3; ++m) g[q][m] = hJ * (S[m] * d0[q] + S[3 + m] * d1[q] + S[6 + m] * d2[q]);
+#endif
     const float mu = Fn<float>::div(c.mu_inf * T * Fn<float>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     float mu_t = 0.f;
     if (c.sgs) mu_t = rho * eddy_nu(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
@@ -231,8 +259,19 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
   for (int k = K0; k < K1; ++k) {
     const float Sx = S[3 * k], Sy = S[3 * k + 1], Sz = S[3 * k + 2];
     float Fk[4];
+#if VR_PACKED_FACES
+#pragma unroll
+    for (int q = 0; q < 4; q += 2) {
+      float2 t = __fmul2_rn(make_float2(Sx, Sx), make_float2(Fv[0][q], Fv[0][q + 1]));
+      t = __ffma2_rn(make_float2(Sy, Sy), make_float2(Fv[1][q], Fv[1][q + 1]), t);
+      t = __ffma2_rn(make_float2(Sz, Sz), make_float2(Fv[2][q], Fv[2][q + 1]), t);
+      Fk[q] = t.x;
+      Fk[q + 1] = t.y;
+    }
+#else
 #pragma unroll
     for (int q = 0; q < 4; ++q) Fk[q] = Sx * Fv[0][q] + Sy * Fv[1][q] + Sz * Fv[2][q];
+#endif
     // E^k = [rho U, rho u U + S_x p, rho v U + S_y p, rho w U + S_z p, (e + p) U]
     G[k][0] = rho * U[k];
     G[k][1] = m1 * U[k] + Sx * p - Fk[0];
@@ -264,14 +303,36 @@ __device__ __forceinline__ void face_v(const KConst<float>& c, float2 La, float2
   const float e2 = c.k2 * fmaxf(La.y, Lb.y);
   const float e4 = fmaxf(0.f, c.k4 - e2);
   const float l2 = lam * e2, l4 = lam * e4;
-  // (packed FP32x2 pairs for components 0-3 cut 45 instructions per point
-  // here but measured 1% slower: the kernel is not bound by issue alone)
+#if VR_PACKED_FACES
+  // h = (Ga + Gb)/2 - l2 d1 + l4 d3 on component pairs (0, 1) and (2, 3)
+  // with packed FP32x2 operations (each lane rounds as its scalar
+  // counterpart), component 4 in scalar form
+  const float2 m1 = make_float2(-1.f, -1.f), m3 = make_float2(-3.f, -3.f), hf = make_float2(0.5f, 0.5f);
+  const float2 ml2 = make_float2(-l2, -l2), pl4 = make_float2(l4, l4);
+#pragma unroll
+  for (int v = 0; v < 4; v += 2) {
+    const float2 a = make_float2(qa[v], qa[v + 1]), b = make_float2(qb[v], qb[v + 1]);
+    const float2 m = make_float2(qm[v], qm[v + 1]), p = make_float2(qp[v], qp[v + 1]);
+    const float2 d1 = __ffma2_rn(a, m1, b);                       // qb - qa
+    const float2 d3 = __ffma2_rn(d1, m3, __ffma2_rn(m, m1, p));  // (qp - qm) - 3 d1
+    const float2 g = __fmul2_rn(hf, __fadd2_rn(make_float2(Ga[v], Ga[v + 1]), make_float2(Gb[v], Gb[v + 1])));
+    const float2 r = __ffma2_rn(pl4, d3, __ffma2_rn(ml2, d1, g));
+    h[v] = r.x;
+    h[v + 1] = r.y;
+  }
+  {
+    const float d1 = qb[4] - qa[4];
+    const float d3 = (qp[4] - qm[4]) - 3.f * d1;
+    h[4] = fmaf(l4, d3, fmaf(-l2, d1, 0.5f * (Ga[4] + Gb[4])));
+  }
+#else
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const float d1 = qb[v] - qa[v];
     const float d3 = (qp[v] - qm[v]) - 3.f * d1;
     h[v] = 0.5f * (Ga[v] + Gb[v]) - (l2 * d1 - l4 * d3);
   }
+#endif
 }
 
 struct Smem {
