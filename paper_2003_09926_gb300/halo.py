@@ -203,6 +203,8 @@ class HaloExchange:
         mine = set(part.blocks_of(rank))
         if set(self.blocks) != mine:
             raise ValueError(f"rank {rank} owns blocks {sorted(mine)}, given {sorted(self.blocks)}")
+        if not mine:
+            raise ValueError(f"rank {rank} owns no block of the partition (every rank needs one)")
 
     def _on_stream(self):
         if self.stream is None:

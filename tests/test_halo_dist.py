@@ -139,3 +139,8 @@ def test_partition_plan():
     assert halo.split_ranges(10, 3) == [(0, 2), (3, 6), (7, 9)]
     with pytest.raises(ValueError):
         halo.Partition(W.jet_grid(10, 8, 8), [[(0, 4), (6, 9)], [(0, 7)], [(0, 7)]])
+    two = halo.Partition.even(W.jet_grid(20, 10, 10), (2, 1, 1), world=3)
+    with pytest.raises(ValueError):  # rank 2 owns no block
+        halo.HaloExchange(two, 2, {}, halo.LocalTransport())
+    with pytest.raises(ValueError):  # blocks that are not the rank's
+        halo.HaloExchange(two, 0, {1: None}, halo.LocalTransport())
