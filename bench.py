@@ -282,6 +282,7 @@ def riemann_branch(q, n, gamma=1.4, margin=False):
 # 200 steps (max |FP32 - FP64| relative to max|v|, worst variable)
 FP32_CLASS_BOUNDS = {"interior_d3plus": 5e-5, "interior_d2": 1e-4, "interior_d1": 5e-4, "inflow_face": 1e-6,
                      "farfield_face_clear_of_switch": 5e-4, "farfield_face_near_switch": 0.2}
+FP32_BOUNDS_STEPS = 200
 
 
 # Far-field face nodes closer than this (in velocity units, c_inf = 1) to a
@@ -706,8 +707,12 @@ def main(argv=None):
             "max_rel_all_nodes": max(float(np.abs(Q[v] - Qref[v]).max() / np.abs(Qref[v]).max()) for v in range(5)),
             "l2_rel": max(float(np.sqrt(np.mean((Q[v] - Qref[v]) ** 2) / np.mean(Qref[v] ** 2))) for v in range(5)),
             "classes": error_classes(Q, Qref, Sref, grid["bc"])}
+        # the bounds are stated for the configuration's run length: after a
+        # few steps the transverse momenta are still near zero, and errors
+        # relative to their maxima read larger
         errors[W.PRECISION_NAMES[prec]]["within_stated_bounds"] = all(
-            errors[W.PRECISION_NAMES[prec]]["classes"][k]["max_rel"] <= b for k, b in FP32_CLASS_BOUNDS.items())
+            errors[W.PRECISION_NAMES[prec]]["classes"][k]["max_rel"] <= b
+            for k, b in FP32_CLASS_BOUNDS.items()) if err_steps == FP32_BOUNDS_STEPS else None
         del g
     del Qref, Sref
 
@@ -798,7 +803,7 @@ def main(argv=None):
             "variants": {W.PRECISION_NAMES[p]: r for p, r in results.items()},
             "fp32_error_vs_fp64": {"steps": err_steps, "per_mode": errors,
                                    "interior": "nodes at least 3 from every face",
-                                   "stated_bounds": FP32_CLASS_BOUNDS,
+                                   "stated_bounds": FP32_CLASS_BOUNDS, "bounds_steps": FP32_BOUNDS_STEPS,
                                    "classes": "every node by class: inflow face; far-field face nodes whose Riemann branch (supersonic in / subsonic outside entropy / subsonic inside entropy / supersonic out, from the adjacent interior node) is the same in both precisions and at least 2e-4 from every switch, and the others (near a switch: the two precisions may decide differently); nodes at distance 1, 2 and >= 3 from the nearest face"},
             "fp64_vs_fp32_speedup": results[head]["value"] / results[W.P64]["value"]}
     if not args.no_batched:

@@ -218,6 +218,7 @@ struct jz_batch {
   char* dev = nullptr;
   size_t off_stage = 0, off_bc = 0, off_rate = 0, off_items = 0, off_queue = 0, off_bcitems = 0;
   int nitems = 0, nbcitems = 0;
+  int model = 0;                // stage kernel flow model shared by every grid (else the runtime model)
   bool cyl = false;             // some grid is cylindrical (centreline means before each boundary pass)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -999,8 +1000,9 @@ int enqueue_batch_step(jz_batch* b, double cfl) {
   if (e != cudaSuccess) return fail(JZ_ECUDA, "batched time step launch failed: %s", cudaGetErrorString(e));
   const int src[5] = {0, 1, 2, 1, 2}, out[5] = {1, 2, 1, 2, 0};
   for (int l = 0; l < 5; ++l) {
-    e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, grid_tiling(b->grids[0]->dev), b->dev + b->off_stage, (const int4*)(b->dev + b->off_items), b->nitems,
-                           (unsigned int*)(b->dev + b->off_queue), l, src[l], out[l], s);
+    e = launch_stage_batch(b->prec, b->grids[0]->dev.variant, grid_tiling(b->grids[0]->dev), b->dev + b->off_stage,
+                           (const int4*)(b->dev + b->off_items), b->nitems, (unsigned int*)(b->dev + b->off_queue), l,
+                           src[l], out[l], b->model, s);
     if (e != cudaSuccess) return fail(JZ_ECUDA, "batched stage launch failed: %s", cudaGetErrorString(e));
     e = launch_bc_batch(b->prec, b->dev + b->off_bc, n, (const int4*)(b->dev + b->off_bcitems), b->nbcitems, out[l],
                         b->cyl, s);
@@ -1046,6 +1048,9 @@ int create_batch(jz_grid* const* grids, int n, bool coupled, void* dev_buf, size
   b->off_bcitems = P.off_bcitems;
   b->nbcitems = (int)P.bcitems.size();
   for (int k = 0; k < n; ++k) b->cyl = b->cyl || grids[k]->dev.L.cyl;
+  b->model = stage_model(grids[0]->dev);
+  for (int k = 1; k < n; ++k)
+    if (stage_model(grids[k]->dev) != b->model) b->model = 0;  // the runtime model serves a mix
   b->coupled = coupled;
   b->off_x = P.off_x;
   for (int d = 0; d < 3; ++d) {

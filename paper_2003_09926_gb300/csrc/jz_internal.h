@@ -129,8 +129,13 @@ cudaError_t launch_stage(const GridDev& g, int stage, int qsel, int qout, cudaSt
 // batched stage: a device table of per-grid stage contexts and work items
 size_t stage_ctx_bytes(int prec);
 void stage_ctx_fill(void* host_dst, const GridDev& g);
+// the flow model a grid's FP32 vector-record stage kernel is compiled for
+// (the runtime model when none of the constant-flag builds matches)
+int stage_model(const GridDev& g);
+// model: the stage_model shared by every grid of the batch, else the runtime model
 cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const void* ctx, const int4* items,
-                               int nitems, unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s);
+                               int nitems, unsigned int* queue, int stage, int qsel, int qout, int model,
+                               cudaStream_t s);
 cudaError_t stage_configure();  // one-time kernel attributes (dynamic shared memory)
 
 }  // namespace jz

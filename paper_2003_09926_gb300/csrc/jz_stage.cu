@@ -689,13 +689,16 @@ void stage_ctx_fill(void* dst, const GridDev& g) {
   }
 }
 
+int stage_model(const GridDev& g) { return flow_model(make_kconst<float>(g.F)); }
+
 cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const void* ctx, const int4* items,
-                               int nitems, unsigned int* queue, int stage, int qsel, int qout, cudaStream_t s) {
+                               int nitems, unsigned int* queue, int stage, int qsel, int qout, int model,
+                               cudaStream_t s) {
   if (prec == JZ_P32 && variant == 2) {
     const StageSel st{kRkAlpha[stage], qsel, qout, 0};
-    if (tile.ti == 16 && tile.tj == 32) return launch_stage_v_batch_16x32(ctx, items, nitems, queue, st, s);
-    if (tile.ti == 16 && tile.tj == 16) return launch_stage_v_batch_16x16(ctx, items, nitems, queue, st, s);
-    return launch_stage_v_batch_32x16(ctx, items, nitems, queue, st, s);
+    if (tile.ti == 16 && tile.tj == 32) return launch_stage_v_batch_16x32(ctx, items, nitems, queue, st, model, s);
+    if (tile.ti == 16 && tile.tj == 16) return launch_stage_v_batch_16x16(ctx, items, nitems, queue, st, model, s);
+    return launch_stage_v_batch_32x16(ctx, items, nitems, queue, st, model, s);
   }
   switch (prec) {
     case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);

@@ -48,6 +48,45 @@ __host__ __device__ inline KConst<R> make_kconst(const FlowC& F) {
 template <typename R>
 __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 
+// Flow models that the FP32 vector-record stage kernel is compiled for with
+// constant flags: the stage body of each model carries no branch on the
+// flags of the others, so that the compiler schedules the viscous, eddy
+// viscosity and dissipation arithmetic of a node as one block.  The runtime
+// model reads the flags of KConst and serves every other combination; the
+// arithmetic of a node is the same expression in every build.
+constexpr int kModelRuntime = 0;      // flags read at run time
+constexpr int kModelSmagorinsky = 1;  // viscous, Smagorinsky eddy viscosity, sigma = 1/2
+constexpr int kModelVreman = 2;       // viscous, Vreman eddy viscosity, sigma = 1/2
+constexpr int kModelEuler = 3;        // inviscid, sigma = 1/2
+constexpr int kModels = 4;
+
+template <typename R>
+__host__ __device__ inline int flow_model(const KConst<R>& c) {
+  if (!c.sig_half) return kModelRuntime;
+  if (!c.viscous) return kModelEuler;
+  if (!c.sgs) return kModelRuntime;
+  return c.vreman ? kModelVreman : kModelSmagorinsky;
+}
+
+// The flags of model MD: compile-time constants, except for the runtime model.
+template <int MD>
+struct ModelFlags {
+  template <typename R>
+  static __device__ __forceinline__ bool viscous(const KConst<R>& c) {
+    return MD == kModelRuntime ? c.viscous != 0 : MD != kModelEuler;
+  }
+  template <typename R>
+  static __device__ __forceinline__ bool sgs(const KConst<R>& c) {
+    return MD == kModelRuntime ? c.sgs != 0 : MD != kModelEuler;
+  }
+  template <typename R>
+  static __device__ __forceinline__ bool sig_half(const KConst<R>& c) {
+    return MD == kModelRuntime ? c.sig_half != 0 : true;
+  }
+  // eddy viscosity model: -1 read at run time, 0 Smagorinsky, 1 Vreman
+  static constexpr int eddy = MD == kModelRuntime ? -1 : (MD == kModelVreman ? 1 : 0);
+};
+
 // Eddy viscosity mu_t / rho from the velocity gradients g[a][m] = du_a/dx_m
 // and J (Delta^2 = J^(-2/3)).
 //   Smagorinsky: (C_s Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij).
@@ -59,9 +98,10 @@ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 //     FP32 the reciprocal flushes subnormal operands to zero, so there the
 //     model is also taken as 0 where g_am g_am is below the smallest normal
 //     FP32 number; FP64 uses the plain > 0 test.
-template <typename R>
+// EDDY: -1 the model of c (read at run time), 0 Smagorinsky, 1 Vreman.
+template <typename R, int EDDY = -1>
 __device__ __forceinline__ R eddy_nu(const KConst<R>& c, const R g[4][3], R Jn) {
-  if (c.vreman) {
+  if (EDDY < 0 ? c.vreman != 0 : EDDY == 1) {
     const R tiny = sizeof(R) == 4 ? R(1.17549435e-38f) : R(0);
     R b[3][3];
 #pragma unroll
@@ -210,7 +250,7 @@ constexpr int vr_ctas_per_sm(int ti, int tj) { return ti * tj <= 256 ? 2 : 1; }
   cudaError_t stage_v_configure_##S();                                                                        \
   cudaError_t launch_stage_v_##S(const stg::StageCtx<float, float>& X, const stg::StageSel& st, cudaStream_t s); \
   cudaError_t launch_stage_v_batch_##S(const void* ctx, const int4* items, int nitems, unsigned int* queue,      \
-                                       const stg::StageSel& st, cudaStream_t s);
+                                       const stg::StageSel& st, int model, cudaStream_t s);
 JZ_STAGE_V_DECL(32x16)
 JZ_STAGE_V_DECL(16x32)
 JZ_STAGE_V_DECL(16x16)

@@ -165,7 +165,7 @@ __device__ __forceinline__ bool wait_v(uint64_t* bar, uint32_t parity, long long
 // nu^k.  Primitive records of the planes below / at / above in slots sM, sC,
 // sP; the conserved record of the plane in slot qC.  DIR = 0: all three
 // directions; DIR = 1 / 2 / 3: direction i / j / k only.
-template <int DIR>
+template <int DIR, int MD>
 __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const float* __restrict__ PP,
                                        const float4* __restrict__ QV, const float* __restrict__ QE,
                                        const float* __restrict__ met, int sM, int sC, int sP, int qC, int x, int y,
@@ -191,7 +191,7 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int q = 0; q < 4; ++q) Fv[m][q] = 0.f;
-  if (c.viscous) {
+  if (ModelFlags<MD>::viscous(c)) {
     // Cartesian gradients of u, v, w, T: J/2 sum_k S^k_m (phi_+ - phi_-)
     const float4 a0 = pc[o + 1], b0 = pc[o - 1], a1 = pc[o + RR], b1 = pc[o - RR];
     const float4 a2 = PV[sP + o], b2 = PV[sM + o];
@@ -229,7 +229,7 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
 #endif
     const float mu = Fn<float>::div(c.mu_inf * T * Fn<float>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     float mu_t = 0.f;
-    if (c.sgs) mu_t = rho * eddy_nu(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
+    if (ModelFlags<MD>::sgs(c)) mu_t = rho * eddy_nu<float, ModelFlags<MD>::eddy>(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
     const float mue = mu + mu_t;
     const float kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
     const float div3 = (g[0][0] + g[1][1] + g[2][2]) * (2.f / 3.f);
@@ -250,7 +250,7 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
     lam[k] = fabsf(U[k]) + cson * sn;
   }
   float sq[3] = {0.f, 0.f, 0.f};
-  if (c.sig_half) {
+  if (ModelFlags<MD>::sig_half(c)) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) sq[k] = Fn<float>::sqrt_(lam[k]);
   }
@@ -279,7 +279,7 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
     G[k][3] = m3 * U[k] + Sz * p - Fk[2];
     G[k][4] = (e + p) * U[k] - Fk[3];
     const int a = (k + 1) % 3, b = (k + 2) % 3;
-    if (c.sig_half)  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
+    if (ModelFlags<MD>::sig_half(c))  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
       lt[k] = lam[k] + sq[k] * (sq[a] + sq[b]);
     else
       lt[k] = lam[k] > 0.f ? lam[k] * (1.f + Fn<float>::powp(Fn<float>::div(lam[a], lam[k]), c.sigma) +
@@ -380,6 +380,7 @@ struct Own {
 // every wait follows from the plane index.  On a bounded-wait timeout the
 // item records where it gave up, lets its copies in flight land and returns
 // false.
+template <int MD>
 __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const StageSel& st, int bx, int by, int bz,
                                        unsigned char* smem, bool first) {
   using namespace vr;
@@ -513,7 +514,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
     const int sM = pslot(kk - 1), sC = pslot(kk), sP = pslot(kk + 1), qC = slot(kk);
     float G[3][5], lt[3], nu[3];
     if (role == 0) {
-      node_v<0>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jn);
+      node_v<0, MD>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         w.Gi[v] = G[0][v];
@@ -530,7 +531,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       nu3 = nu[2];
     } else if (role == 1) {
       float Jh;
-      node_v<1>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
+      node_v<1, MD>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { w.Gi[v] = G[0][v]; w.Gj[v] = 0.f; }
       w.Li = make_float2(lt[0], nu[0]);
@@ -539,7 +540,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       sm.Li[ny * GIW + nx + 1] = w.Li;
     } else {
       float Jh;
-      node_v<2>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
+      node_v<2, MD>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, sM, sC, sP, qC, nx, ny, c, G, lt, nu, Jh);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { w.Gj[v] = G[1][v]; w.Gi[v] = 0.f; }
       w.Lj = make_float2(lt[1], nu[1]);
@@ -553,7 +554,7 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   auto node_pass_k = [&](int kk, float G3[5], float& lt3, float& nu3, float& Jn) {
     if (role != 0) return;
     float G[3][5], lt[3], nu[3];
-    node_v<3>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, pslot(kk - 1), pslot(kk), pslot(kk + 1), slot(kk), nx, ny, c, G,
+    node_v<3, MD>(sm.PV, sm.PP, sm.QV, sm.QE, sm.met, pslot(kk - 1), pslot(kk), pslot(kk + 1), slot(kk), nx, ny, c, G,
               lt, nu, Jn);
 #pragma unroll
     for (int v = 0; v < 5; ++v) G3[v] = G[2][v];
@@ -762,12 +763,14 @@ fail:
   return false;
 }
 
+template <int MD>
 __global__ void __launch_bounds__(vr::NT, vr::MINB)
     k_stage_v(const __grid_constant__ StageCtx<float, float> X, const StageSel st) {
   extern __shared__ __align__(128) unsigned char smem[];
-  item_v(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true);
+  item_v<MD>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true);
 }
 
+template <int MD>
 __global__ void __launch_bounds__(vr::NT, vr::MINB)
     k_stage_v_batch(const StageCtx<float, float>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
                     unsigned int* queue, const StageSel st) {
@@ -781,35 +784,59 @@ __global__ void __launch_bounds__(vr::NT, vr::MINB)
     __syncthreads();
     if (it >= nitems) break;
     const int4 w = items[it];
-    if (!item_v(ctx[w.x], st, w.y, w.z, w.w, smem, first)) break;
+    if (!item_v<MD>(ctx[w.x], st, w.y, w.z, w.w, smem, first)) break;
     first = false;
   }
+}
+
+template <int MD>
+cudaError_t configure_model() {
+  cudaError_t e = cudaFuncSetAttribute(k_stage_v<MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage_v_batch<MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
 }
 
 }  // namespace
 
 cudaError_t VR_FN(stage_v_configure)() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage_v_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vr::BYTES);
+  cudaError_t e;
+  if ((e = configure_model<kModelRuntime>()) != cudaSuccess) return e;
+  if ((e = configure_model<kModelSmagorinsky>()) != cudaSuccess) return e;
+  if ((e = configure_model<kModelVreman>()) != cudaSuccess) return e;
+  return configure_model<kModelEuler>();
 }
 
 cudaError_t VR_FN(launch_stage_v)(const StageCtx<float, float>& X, const StageSel& st, cudaStream_t s) {
   const Layout& L = X.L;
   const int nz = L.hi[2] - L.lo[2] + 1;
   dim3 grid((L.hi[0] + vr::TI) / vr::TI, (L.hi[1] + vr::TJ) / vr::TJ, (nz + X.kc - 1) / X.kc);
-  k_stage_v<<<grid, vr::NT, vr::BYTES, s>>>(X, st);
+  switch (flow_model(X.k)) {
+    case kModelSmagorinsky: k_stage_v<kModelSmagorinsky><<<grid, vr::NT, vr::BYTES, s>>>(X, st); break;
+    case kModelVreman: k_stage_v<kModelVreman><<<grid, vr::NT, vr::BYTES, s>>>(X, st); break;
+    case kModelEuler: k_stage_v<kModelEuler><<<grid, vr::NT, vr::BYTES, s>>>(X, st); break;
+    default: k_stage_v<kModelRuntime><<<grid, vr::NT, vr::BYTES, s>>>(X, st); break;
+  }
   count_launches(1);
   return cudaGetLastError();
 }
 
+// model: the flow model every grid of the batch shares (kModelRuntime when
+// they differ)
 cudaError_t VR_FN(launch_stage_v_batch)(const void* ctx, const int4* items, int nitems, unsigned int* queue,
-                                        const StageSel& st, cudaStream_t s) {
+                                        const StageSel& st, int model, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const int slots = device_sm_count() * vr::MINB;
   const int ctas = nitems < slots ? nitems : slots;
-  k_stage_v_batch<<<ctas, vr::NT, vr::BYTES, s>>>((const StageCtx<float, float>*)ctx, items, nitems, queue, st);
+  const auto* X = (const StageCtx<float, float>*)ctx;
+  switch (model) {
+    case kModelSmagorinsky:
+      k_stage_v_batch<kModelSmagorinsky><<<ctas, vr::NT, vr::BYTES, s>>>(X, items, nitems, queue, st);
+      break;
+    case kModelVreman: k_stage_v_batch<kModelVreman><<<ctas, vr::NT, vr::BYTES, s>>>(X, items, nitems, queue, st); break;
+    case kModelEuler: k_stage_v_batch<kModelEuler><<<ctas, vr::NT, vr::BYTES, s>>>(X, items, nitems, queue, st); break;
+    default: k_stage_v_batch<kModelRuntime><<<ctas, vr::NT, vr::BYTES, s>>>(X, items, nitems, queue, st); break;
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -48,6 +48,33 @@ def test_batch_equals_grids_alone(jz, prec):
     b.close()
 
 
+def test_mixed_flow_models_equal_their_own_builds(jz):
+    """The FP32 vector-record stage kernel is compiled once per flow model
+    with constant flags (Smagorinsky, Vreman, inviscid, all with sigma = 1/2)
+    and once with the flags read at run time.  A batch whose grids differ in
+    model runs the runtime build; stepped alone, each grid runs its own
+    build (the runtime one for the laminar and sigma != 1/2 flows).  The
+    states must agree bitwise: the builds differ in branches, not in the
+    arithmetic of a node."""
+    import torch
+    flows = [W.jet_flow(), W.jet_flow(re=5e3, sgs=W.SGS_VREMAN), W.jet_flow(re=0.0, cs=0.0),
+             W.jet_flow(re=4e3, cs=0.0), W.jet_flow(sigma=0.7)]
+    shapes = [(36, 22, 18), (33, 17, 19), (40, 24, 20), (20, 18, 12), (24, 20, 14)]
+    cases = [(W.jet_grid(*sh, map_amp=0.03, map_seed=k, precision=W.P32), f, 40 + k)
+             for k, (sh, f) in enumerate(zip(shapes, flows))]
+    stream = torch.cuda.Stream()
+    batch_grids = [jz.Grid(g, stream=stream).init(f, s) for g, f, s in cases]
+    b = jz.Batch(batch_grids, stream=stream)
+    b.nsteps(4, cfl=0.5)
+    stream.synchronize()
+    for (g, f, s), bg in zip(cases, batch_grids):
+        alone = jz.Grid(g).init(f, s)
+        alone.nsteps(4, cfl=0.5)
+        np.testing.assert_array_equal(bg.download(), alone.download())
+        alone.close()
+    b.close()
+
+
 def test_batch_rejects_mixed_precision(jz):
     import torch
     s = torch.cuda.Stream()
