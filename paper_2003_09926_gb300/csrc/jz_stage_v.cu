@@ -375,12 +375,21 @@ struct Own {
   float2 Li, Lj;       // (lambda~, nu) in i and j
 };
 
-// One work item: tile (bx, by), k-chunk bz of grid X, stage st.  The CTA's
+// Node role of thread tid (warps hold one role each): 0 tile node, 2 j-halo
+// node, 1 i-halo node.
+__device__ __forceinline__ int role_of(int tid) {
+  return tid < vr::NTILE ? 0 : (tid < vr::NTILE + vr::NJH ? 2 : 1);
+}
+
+// One work item: tile (bx, by), k-chunk bz of grid X, stage st, for the
+// threads of node role ROLE (each role runs its own instantiation of the
+// plane march, without branches on the role; all roles pass the same
+// sequence of block barriers).  The CTA's
 // mbarriers are (re)initialised at the start of every item, so the parity of
 // every wait follows from the plane index.  On a bounded-wait timeout the
 // item records where it gave up, lets its copies in flight land and returns
 // false.
-template <int MD>
+template <int MD, int ROLE>
 __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const StageSel& st, int bx, int by, int bz,
                                        unsigned char* smem, bool first) {
   using namespace vr;
@@ -395,10 +404,11 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
   const uint32_t xtx = st.stall ? kStallBytes : 0u;
   const long long wlim = st.stall ? kStallLimit : kWaitLimit;
 
-  // node role: tile node, j-halo node (rows -1, TJ) or i-halo node (columns -1, TI)
-  int nx, ny, role;
-  if (tid < NTILE) {
-    role = 0;
+  // node role of this thread, a constant of the instantiation: 0 tile node,
+  // 2 j-halo node (rows -1, TJ), 1 i-halo node (columns -1, TI)
+  constexpr int role = ROLE;
+  int nx, ny;
+  if constexpr (ROLE == 0) {
     if (ROWS4) {  // warp w: rows (w & 3) + 8 (w >> 2) and 4 below it
       const int w = tid >> 5, l = tid & 31;
       nx = l & 15;
@@ -407,10 +417,11 @@ __device__ __forceinline__ bool item_v(const StageCtx<float, float>& X, const St
       nx = tid % TI;
       ny = tid / TI;
     }
-  }
-  else if (tid < NTILE + NJH) { role = 2; const int h = tid - NTILE; nx = h % TI; ny = (h / TI) ? TJ : -1; }
-  else {
-    role = 1;
+  } else if constexpr (ROLE == 2) {
+    const int h = tid - NTILE;
+    nx = h % TI;
+    ny = (h / TI) ? TJ : -1;
+  } else {
     const int h = tid - NTILE - NJH;
     if (ROWS4) {  // both halo columns of four rows per quarter-warp: 2-way, not 4-way, bank conflicts
       ny = h >> 1;
@@ -767,7 +778,11 @@ template <int MD>
 __global__ void __launch_bounds__(vr::NT, vr::MINB)
     k_stage_v(const __grid_constant__ StageCtx<float, float> X, const StageSel st) {
   extern __shared__ __align__(128) unsigned char smem[];
-  item_v<MD>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true);
+  switch (role_of(threadIdx.x)) {
+    case 0: item_v<MD, 0>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true); break;
+    case 2: item_v<MD, 2>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true); break;
+    default: item_v<MD, 1>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, true); break;
+  }
 }
 
 template <int MD>
@@ -784,7 +799,13 @@ __global__ void __launch_bounds__(vr::NT, vr::MINB)
     __syncthreads();
     if (it >= nitems) break;
     const int4 w = items[it];
-    if (!item_v<MD>(ctx[w.x], st, w.y, w.z, w.w, smem, first)) break;
+    bool ok;
+    switch (role_of(threadIdx.x)) {
+      case 0: ok = item_v<MD, 0>(ctx[w.x], st, w.y, w.z, w.w, smem, first); break;
+      case 2: ok = item_v<MD, 2>(ctx[w.x], st, w.y, w.z, w.w, smem, first); break;
+      default: ok = item_v<MD, 1>(ctx[w.x], st, w.y, w.z, w.w, smem, first); break;
+    }
+    if (!ok) break;
     first = false;
   }
 }
