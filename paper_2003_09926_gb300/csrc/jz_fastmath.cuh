@@ -23,6 +23,8 @@ template <> struct Fn<float> {
     return y;
   }
   static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
+  // a product that is never fused into a later addition
+  static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
   // x^e = 2^(e log2 x) for x > 0 (no library call inside the flux code)
   static __device__ __forceinline__ float powp(float x, float e) {
     float l, y;
@@ -44,6 +46,7 @@ template <> struct Fn<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double powp(double x, double e) { return pow(x, e); }
   static __device__ __forceinline__ double jm23(double J) {
     const double cb = cbrt(J);

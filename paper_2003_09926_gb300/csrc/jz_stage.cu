@@ -98,7 +98,7 @@ __device__ __forceinline__ R ring_at(const R* ring, int slot, int var, int y, in
 // Node quantities of node (x, y) of the centre plane (ring slot sC; the
 // planes below / above in sM / sP): G^k = E^k - F^k, lambda~^k and nu^k.
 // DIR = 0: all three directions; DIR = 1 / 2: direction i / j only.
-template <typename R, typename MT, int RW, int PL, int DIR>
+template <typename R, typename MT, int RW, int PL, int DIR, int MD>
 __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* __restrict__ met, int sM, int sC, int sP,
                                           int x, int y, const KConst<R>& c, R G[3][5], R lt[3], R nu[3], R& Jn) {
   const int lx = x + 2, ly = y + 2, o = ly * RW + lx;
@@ -118,7 +118,7 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
   for (int m = 0; m < 3; ++m)
 #pragma unroll
     for (int q = 0; q < 4; ++q) Fv[m][q] = R(0);
-  if (c.viscous) {
+  if (ModelFlags<MD>::viscous(c)) {
     const int var[4] = {V_U, V_V, V_W, V_T};
     R g[4][3];  // Cartesian gradients of u, v, w, T: J/2 sum_k S^k_m (phi_+ - phi_-)
     const R hJ = R(0.5) * Jn;
@@ -132,7 +132,9 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     }
     const R mu = Fn<R>::div(c.mu_inf * T * Fn<R>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     R mu_t = R(0);
-    if (c.sgs) mu_t = rho * eddy_nu(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
+    // Smagorinsky or Vreman, Delta = J^(-1/3); an unfused product, so that
+    // mu + mu_t rounds alike in the constant-flag and runtime-flag builds
+    if (ModelFlags<MD>::sgs(c)) mu_t = Fn<R>::mul_rn(rho, eddy_nu<R, ModelFlags<MD>::eddy>(c, g, Jn));
     const R mue = mu + mu_t;
     const R kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
     const R div3 = (g[0][0] + g[1][1] + g[2][2]) * R(2.0 / 3.0);
@@ -153,7 +155,7 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     lam[k] = fabs(U[k]) + cson * sn;
   }
   R sq[3] = {R(0), R(0), R(0)};
-  if (c.sig_half) {
+  if (ModelFlags<MD>::sig_half(c)) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) sq[k] = Fn<R>::sqrt_(lam[k]);
   }
@@ -171,7 +173,7 @@ __device__ __forceinline__ void node_flux(const R* __restrict__ ring, const MT* 
     G[k][3] = m3 * U[k] + Sz * p - Fk[2];
     G[k][4] = (e + p) * U[k] - Fk[3];
     const int a = (k + 1) % 3, b = (k + 2) % 3;
-    if (c.sig_half)  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
+    if (ModelFlags<MD>::sig_half(c))  // lambda (1 + (la/l)^1/2 + (lb/l)^1/2) = lambda + sqrt(lambda) (sqrt(la) + sqrt(lb))
       lt[k] = lam[k] + sq[k] * (sq[a] + sq[b]);
     else
       lt[k] = lam[k] > R(0) ? lam[k] * (R(1) + Fn<R>::powp(Fn<R>::div(lam[a], lam[k]), c.sigma) +
@@ -225,7 +227,7 @@ __device__ __forceinline__ void face5(const R* ring, const int so[4], const int 
 // update adds the FP32 increment to it in FP64, stages 1-4 round their
 // output to FP32 (it feeds only the FP32 flux evaluation), and stage 5 writes
 // both the FP64 state and its FP32 copy (the next step's flux input).
-template <typename R, typename MT, int TI, int TJ, bool S64 = false>
+template <typename R, typename MT, int TI, int TJ, bool S64, int MD>
 __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const StageSel& st, int bx, int by, int bz,
                                            unsigned char* smem, uint32_t ph[3], int issued[3], int waited[3],
                                            bool& failed) {
@@ -340,7 +342,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
     const int sM = (kk + 7) & 3, sC = (kk + 8) & 3, sP = (kk + 9) & 3;
     R G[3][5], lt[3], nu[3];
     if (role == 0) {
-      node_flux<R, MT, RW, PL, 0>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jn);
+      node_flux<R, MT, RW, PL, 0, MD>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         Gi[(v * TJ + ny) * (TI + 2) + nx + 1] = G[0][v];
@@ -355,7 +357,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
       nu3 = nu[2];
     } else if (role == 1) {
       R Jh;
-      node_flux<R, MT, RW, PL, 1>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+      node_flux<R, MT, RW, PL, 1, MD>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
       const int col = nx + 1;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Gi[(v * TJ + ny) * (TI + 2) + col] = G[0][v];
@@ -363,7 +365,7 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
       Li[(1 * TJ + ny) * (TI + 2) + col] = nu[0];
     } else {
       R Jh;
-      node_flux<R, MT, RW, PL, 2>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
+      node_flux<R, MT, RW, PL, 2, MD>(ring, met, sM, sC, sP, nx, ny, c, G, lt, nu, Jh);
       const int row = ny + 1;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Gj[(v * (TJ + 2) + row) * TI + nx] = G[1][v];
@@ -514,8 +516,9 @@ __device__ __forceinline__ void stage_item(const StageCtx<R, MT>& X, const Stage
 
 }
 
-// One grid: one CTA per (tile, k-chunk).
-template <typename R, typename MT, int TI, int TJ, bool S64 = false>
+// One grid: one CTA per (tile, k-chunk).  MD: the flow model (constant
+// flags, or read at run time).
+template <typename R, typename MT, int TI, int TJ, bool S64, int MD>
 __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage(const __grid_constant__ StageCtx<R, MT> X, const StageSel st) {
   using C = Cfg<R, MT, TI, TJ>;
@@ -525,13 +528,17 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
   uint32_t ph[3] = {0, 0, 0};
   int issued[3] = {0, 0, 0}, waited[3] = {0, 0, 0};
   bool failed = false;
-  stage_item<R, MT, TI, TJ, S64>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
+  stage_item<R, MT, TI, TJ, S64, MD>(X, st, blockIdx.x, blockIdx.y, blockIdx.z, smem, ph, issued, waited, failed);
   if (failed) drain_after_timeout(bar, X.err, issued, waited, st.stall ? kStallBytes : 0u);
 }
 
 // Many grids: persistent CTAs (one per SM) take work items (grid, tile,
 // k-chunk) from a device queue, largest first.
-template <typename R, typename MT, int TI, int TJ, bool S64 = false>
+// MD: the flow model every grid of the batch shares (kModelSmagorinsky), or
+// kMixedModels: each work item in the build of its own grid's model, as
+// when the grid is stepped alone.
+constexpr int kMixedModels = -1;
+template <typename R, typename MT, int TI, int TJ, bool S64, int MD>
 __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MINB)
     k_stage_batch(const StageCtx<R, MT>* __restrict__ ctx, const int4* __restrict__ items, int nitems,
                   unsigned int* queue, const StageSel st) {
@@ -552,7 +559,10 @@ __global__ void __launch_bounds__(Cfg<R, MT, TI, TJ>::NT, Cfg<R, MT, TI, TJ>::MI
     if (it >= nitems) break;
     const int4 w = items[it];
     gsel = w.x;
-    stage_item<R, MT, TI, TJ, S64>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
+    if (MD == kModelSmagorinsky || (MD == kMixedModels && flow_model(ctx[w.x].k) == kModelSmagorinsky))
+      stage_item<R, MT, TI, TJ, S64, kModelSmagorinsky>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
+    else
+      stage_item<R, MT, TI, TJ, S64, kModelRuntime>(ctx[w.x], st, w.y, w.z, w.w, smem, ph, issued, waited, failed);
     if (failed) break;
   }
   if (failed) drain_after_timeout(bar, ctx[gsel].err, issued, waited, st.stall ? kStallBytes : 0u);
@@ -565,13 +575,24 @@ constexpr int TI32 = 32, TJ32 = 16;  // P32: 608 threads, 191 KB: one CTA per SM
 constexpr int TIM = 32, TJM = 16;    // P32_M64: 608 threads, 220 KB (FP64 metric staging): one CTA per SM
 constexpr int TI64 = 16, TJ64 = 16;  // FP64: 320 threads, 207 KB
 
+// The scalar kernels are built for two flow models: the configurations'
+// (Smagorinsky, sigma = 1/2) with constant flags, and every other with the
+// flags read at run time.  The two builds may fuse a multiplication into an
+// addition differently, so a batch of grids that do not all take the
+// Smagorinsky build runs every grid in the build of its own model (both are
+// inlined into that kernel): a grid's state is bitwise the one it reaches
+// alone.
 template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t configure_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Cfg<R, MT, TI, TJ>::BYTES);
+  const int bytes = (int)Cfg<R, MT, TI, TJ>::BYTES;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ, S64, kModelRuntime>, a, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ, S64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Cfg<R, MT, TI, TJ>::BYTES);
+  e = cudaFuncSetAttribute(k_stage<R, MT, TI, TJ, S64, kModelSmagorinsky>, a, bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ, S64, kModelSmagorinsky>, a, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage_batch<R, MT, TI, TJ, S64, kMixedModels>, a, bytes);
 }
 
 
@@ -603,21 +624,28 @@ cudaError_t launch_one(const GridDev& g, int stage, int qsel, int qout, cudaStre
   const StageSel st{kRkAlpha[stage], qsel, qout, g.stall_test};
   const int nz = g.L.hi[2] - g.L.lo[2] + 1;
   dim3 grid((g.L.hi[0] + TI) / TI, (g.L.hi[1] + TJ) / TJ, (nz + g.kc - 1) / g.kc);
-  k_stage<R, MT, TI, TJ, S64><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
+  if (flow_model(X.k) == kModelSmagorinsky)
+    k_stage<R, MT, TI, TJ, S64, kModelSmagorinsky><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
+  else
+    k_stage<R, MT, TI, TJ, S64, kModelRuntime><<<grid, Cf::NT, Cf::BYTES, s>>>(X, st);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <typename R, typename MT, int TI, int TJ, bool S64 = false>
 cudaError_t launch_batch(const void* ctx, const int4* items, int nitems, unsigned int* queue, int stage, int qsel,
-                         int qout, cudaStream_t s) {
+                         int qout, int model, cudaStream_t s) {
   using Cf = Cfg<R, MT, TI, TJ>;
   const StageSel st{kRkAlpha[stage], qsel, qout, 0};
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   const int slots = device_sm_count() * Cf::MINB;
   const int ctas = nitems < slots ? nitems : slots;
-  k_stage_batch<R, MT, TI, TJ, S64><<<ctas, Cf::NT, Cf::BYTES, s>>>((const StageCtx<R, MT>*)ctx, items, nitems, queue, st);
+  const auto* X = (const StageCtx<R, MT>*)ctx;
+  if (model == kModelSmagorinsky)
+    k_stage_batch<R, MT, TI, TJ, S64, kModelSmagorinsky><<<ctas, Cf::NT, Cf::BYTES, s>>>(X, items, nitems, queue, st);
+  else
+    k_stage_batch<R, MT, TI, TJ, S64, kMixedModels><<<ctas, Cf::NT, Cf::BYTES, s>>>(X, items, nitems, queue, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -701,11 +729,12 @@ cudaError_t launch_stage_batch(int prec, int variant, StageTiling tile, const vo
     return launch_stage_v_batch_32x16(ctx, items, nitems, queue, st, model, s);
   }
   switch (prec) {
-    case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, s);
-    case JZ_P32_M64: return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, s);
+    case JZ_P64: return launch_batch<double, double, TI64, TJ64>(ctx, items, nitems, queue, stage, qsel, qout, model, s);
+    case JZ_P32_M64:
+      return launch_batch<float, double, TIM, TJM>(ctx, items, nitems, queue, stage, qsel, qout, model, s);
     case JZ_P32_S64:
-      return launch_batch<float, float, TI32, TJ32, true>(ctx, items, nitems, queue, stage, qsel, qout, s);
-    default: return launch_batch<float, float, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, s);
+      return launch_batch<float, float, TI32, TJ32, true>(ctx, items, nitems, queue, stage, qsel, qout, model, s);
+    default: return launch_batch<float, float, TI32, TJ32>(ctx, items, nitems, queue, stage, qsel, qout, model, s);
   }
 }
 

@@ -229,7 +229,9 @@ __device__ __forceinline__ void node_v(const float4* __restrict__ PV, const floa
 #endif
     const float mu = Fn<float>::div(c.mu_inf * T * Fn<float>::sqrt_(T) * c.s1p1, T + c.s1);  // Sutherland
     float mu_t = 0.f;
-    if (ModelFlags<MD>::sgs(c)) mu_t = rho * eddy_nu<float, ModelFlags<MD>::eddy>(c, g, Jn);  // Smagorinsky or Vreman, Delta = J^(-1/3)
+    // Smagorinsky or Vreman, Delta = J^(-1/3); an unfused product, so that
+    // mu + mu_t rounds alike in the constant-flag and runtime-flag builds
+    if (ModelFlags<MD>::sgs(c)) mu_t = Fn<float>::mul_rn(rho, eddy_nu<float, ModelFlags<MD>::eddy>(c, g, Jn));
     const float mue = mu + mu_t;
     const float kap = c.cp * (mu * c.inv_pr + mu_t * c.inv_prt);
     const float div3 = (g[0][0] + g[1][1] + g[2][2]) * (2.f / 3.f);

@@ -48,19 +48,21 @@ def test_batch_equals_grids_alone(jz, prec):
     b.close()
 
 
-def test_mixed_flow_models_equal_their_own_builds(jz):
-    """The FP32 vector-record stage kernel is compiled once per flow model
-    with constant flags (Smagorinsky, Vreman, inviscid, all with sigma = 1/2)
-    and once with the flags read at run time.  A batch whose grids differ in
-    model runs the runtime build; stepped alone, each grid runs its own
-    build (the runtime one for the laminar and sigma != 1/2 flows).  The
-    states must agree bitwise: the builds differ in branches, not in the
-    arithmetic of a node."""
+@pytest.mark.parametrize("prec", [W.P32, W.P64, W.P32_M64, W.P32_S64])
+def test_mixed_flow_models_equal_their_own_builds(jz, prec):
+    """The stage kernels are compiled per flow model with constant flags
+    (FP32 vector-record kernel: Smagorinsky, Vreman, inviscid, all with
+    sigma = 1/2; the scalar kernels of the other modes: Smagorinsky) and once
+    with the flags read at run time.  A batch whose grids differ in model
+    runs the runtime build; stepped alone, each grid runs its own build (the
+    runtime one for the models without a constant-flag build).  The states
+    must agree bitwise: the builds differ in branches, not in the arithmetic
+    of a node."""
     import torch
     flows = [W.jet_flow(), W.jet_flow(re=5e3, sgs=W.SGS_VREMAN), W.jet_flow(re=0.0, cs=0.0),
              W.jet_flow(re=4e3, cs=0.0), W.jet_flow(sigma=0.7)]
     shapes = [(36, 22, 18), (33, 17, 19), (40, 24, 20), (20, 18, 12), (24, 20, 14)]
-    cases = [(W.jet_grid(*sh, map_amp=0.03, map_seed=k, precision=W.P32), f, 40 + k)
+    cases = [(W.jet_grid(*sh, map_amp=0.03, map_seed=k, precision=prec), f, 40 + k)
              for k, (sh, f) in enumerate(zip(shapes, flows))]
     stream = torch.cuda.Stream()
     batch_grids = [jz.Grid(g, stream=stream).init(f, s) for g, f, s in cases]
