@@ -23,6 +23,7 @@ value = points x stages x steps summed over ranks / max rank time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -717,11 +718,14 @@ def main(argv=None):
     del Qref, Sref
 
     # end to end through the public C ABI with host buffers: the initial state
-    # uploaded from pinned host memory, every step's diagnostics (the step's
-    # metric) copied to pinned host memory and read on the host one step
-    # behind (the host enqueues step s+1 before it waits for step s's
-    # record), the final state downloaded
+    # uploaded from pinned host memory; every step's metric -- the
+    # diagnostics (conservation sums, extrema, non-finite count) of the state
+    # the step starts from, formed by the step's own time-step reduction --
+    # copied to pinned host memory and read on the host one step behind (the
+    # host enqueues step s+1 before it waits for step s's record); the final
+    # state's diagnostics by one diagnostics pass; the final state downloaded
     g = jz.Grid(dict(grid, precision=head), device=local).init(cfg["flow"], cfg["seed"] + rank)
+    g.set_step_diagnostics(True)
     host_in = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
     host_out = torch.empty(g.shape, dtype=torch.float64, pin_memory=True).numpy()
     slots = [jz.PinnedDiag(), jz.PinnedDiag()]
@@ -731,13 +735,17 @@ def main(argv=None):
         seen = []
         for s in range(n):
             g.nsteps(1, cfl=cfg["cfl"])
-            g.diagnostics_async(slots[s % 2])
+            g.step_diagnostics_async(slots[s % 2])
             evs[s % 2].record(g.stream)
             if s >= 1:
                 evs[(s - 1) % 2].synchronize()
                 seen.append(slots[(s - 1) % 2].read())
         evs[(n - 1) % 2].synchronize()
         seen.append(slots[(n - 1) % 2].read())
+        g.diagnostics_async(slots[0])  # the state after the last step
+        evs[0].record(g.stream)
+        evs[0].synchronize()
+        seen.append(slots[0].read())
         return seen
 
     g.download(host_in)
@@ -751,15 +759,17 @@ def main(argv=None):
     g.download(host_out)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    assert len(seen) == args.steps and all(d["nonfinite"] == 0 for d in seen)
+    assert len(seen) == args.steps + 1 and all(d["nonfinite"] == 0 for d in seen)
+    assert [d["step"] for d in seen] == list(range(seen[0]["step"], seen[0]["step"] + args.steps + 1))
     e2e_s = reduce_max(torch, e2e_s, world, "cuda")
     state_bytes = host_in.nbytes
-    diag_bytes = 256
+    diag_bytes = ctypes.sizeof(jz.Diag) * len(seen)  # the records copied
     e2e = {"value": weak_value(pts, args.steps, 1e3 * e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / args.steps,
-           "d2h_bytes_per_step": diag_bytes + state_bytes / args.steps,
-           "note": "initial state uploaded from pinned host memory, every step's diagnostics copied to pinned "
-                   "host memory and read one step behind, final state downloaded"}
+           "d2h_bytes_per_step": (diag_bytes + state_bytes) / args.steps,
+           "note": "initial state uploaded from pinned host memory; every step's diagnostics (of the state the "
+                   "step starts from, formed by its time-step reduction) copied to pinned host memory and read "
+                   "one step behind; the final state's diagnostics by one pass; final state downloaded"}
     g.close()
 
     # roofline of the fused stage kernel (dominant kernel) in the headline run

@@ -277,6 +277,28 @@ int jz_diagnostics(jz_grid* g, jz_diag* out);
  * by the next jz_diagnostics.  JZ_EINVAL for a null handle or output. */
 int jz_diagnostics_async(jz_grid* g, jz_diag* out);
 
+/* Diagnostics formed by the steps themselves.  on = 1: the time-step
+ * reduction of every later step with a CFL number (jz_rk_step, jz_nsteps)
+ * also forms the diagnostics of the state it reads -- the state the step
+ * starts from, the previous step's result -- from the same loaded values, so
+ * that no separate pass over the grid is needed; a step with a fixed time
+ * step forms them by the pass of jz_diagnostics.  The record of the last
+ * step is read with jz_step_diagnostics_async.  Its sums are accumulated in
+ * another order than those of jz_diagnostics (equal up to rounding); its
+ * extrema and non-finite count are the same.  The stepping itself is
+ * unchanged.  on = 0 (the default) switches it off.  JZ_EINVAL for other
+ * values of on. */
+int jz_set_step_diagnostics(jz_grid* g, int on);
+
+/* Enqueue on the grid's stream the copy of the grid's latest diagnostics
+ * record to *out, without a pass over the grid: after a step with step
+ * diagnostics on, the diagnostics of the state that step started from
+ * (out->time and out->step name that state, out->dt the step before it).
+ * The rules for *out are those of jz_diagnostics_async.  JZ_EINVAL for a
+ * null handle or output.  jz_diagnostics and jz_diagnostics_async replace
+ * the record with the diagnostics of the current state. */
+int jz_step_diagnostics_async(jz_grid* g, jz_diag* out);
+
 /* Copy the state to host memory: n = 5*ni*nj*nk doubles, layout [v][k][j][i]
  * (conserved rho, rho u, rho v, rho w, e), ghosts excluded; FP32 states are
  * widened (JZ_P32_S64: the updated nodes come from the FP64 state, boundary

@@ -152,7 +152,8 @@ static Carve carve(const jz_grid_desc* d, const int* o0 = nullptr, const int* o1
   c.tab_len += 2 * (size_t)(L.n[2] + 2 * NG);  // azimuth cos / sin
   size_t off = 0;
   c.off_sc = off; off = align256(off + sizeof(Scalars));
-  c.off_partial = off; off = align256(off + sizeof(double) * RED_BLOCKS * DIAG_WORDS);
+  // time-step rate partials, then the diagnostics records (RED_BLOCKS each)
+  c.off_partial = off; off = align256(off + sizeof(double) * RED_BLOCKS * (DIAG_WORDS + 1));
   c.off_tab = off; off = align256(off + sizeof(double) * c.tab_len);
   c.off_inflow = off; off = align256(off + sizeof(double) * (size_t)L.n[1] * (size_t)L.n[2]);
   c.off_axis = off; off = align256(off + sizeof(double) * 5 * (size_t)(L.cyl ? L.n[0] : 1));
@@ -657,6 +658,23 @@ int jz_diagnostics_async(jz_grid* g, jz_diag* out) {
   if (int rc = check_grid(g, true)) return rc;
   if (!out) return fail(JZ_EINVAL, "null output");
   JZ_CUDA(launch_diagnostics(g->dev, g->stream));
+  JZ_CUDA(cudaMemcpyAsync(out, &g->dev.sc->out, sizeof(jz_diag), cudaMemcpyDeviceToHost, g->stream));
+  return JZ_OK;
+}
+
+int jz_set_step_diagnostics(jz_grid* g, int on) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (on != 0 && on != 1) return fail(JZ_EINVAL, "step diagnostics flag must be 0 or 1");
+  if (g->dev.step_diag != on) {
+    g->dev.step_diag = on;
+    drop_graph(g);  // captured launches carry the flag
+  }
+  return JZ_OK;
+}
+
+int jz_step_diagnostics_async(jz_grid* g, jz_diag* out) {
+  if (int rc = check_grid(g, false)) return rc;
+  if (!out) return fail(JZ_EINVAL, "null output");
   JZ_CUDA(cudaMemcpyAsync(out, &g->dev.sc->out, sizeof(jz_diag), cudaMemcpyDeviceToHost, g->stream));
   return JZ_OK;
 }

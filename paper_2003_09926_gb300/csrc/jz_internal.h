@@ -22,7 +22,7 @@ struct GridDev {
   void* M;             // metrics: S^k_m at field 3k+m, J at field 9
   Coords C;            // coordinate tables
   Scalars* sc;         // device scalars
-  double* partial;     // reduction partials: RED_BLOCKS * DIAG_WORDS doubles
+  double* partial;     // reduction partials: RED_BLOCKS * (DIAG_WORDS + 1) doubles
   double* inflow;      // axial inflow velocity at the x- face nodes, [k][j] (set by state_init)
   double* axis;        // centreline values of a cylindrical grid, [5][ni] FP64 (set per boundary pass)
   FlowC F;
@@ -31,6 +31,7 @@ struct GridDev {
   int variant;         // stage kernel of P32: 0 scalar records, 2 vector records
   int vti, vtj;        // tile shape of the vector-record kernel (32 x 16, 16 x 32 or 16 x 16)
   int stall_test;      // test only: the stage kernels' copies wait for bytes that nothing delivers
+  int step_diag;       // each step's time-step reduction also forms the diagnostics of the state it reads
   CUtensorMap tmQ[3];  // TMA maps of Q0, QA, QB (stage kernel tile box)
   CUtensorMap tmM;     // TMA map of the metric fields
   CUtensorMap tmMv;    // the same fields, box of the tile plus a one-node halo (P32)

@@ -52,7 +52,106 @@ __device__ bool last_block(unsigned int* counter) {
   return last;
 }
 
-template <typename ST, typename MT>
+
+// Diagnostics records: [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min,
+// [8] p max, [9] max of the squared Mach number, [10] non-finite count.
+// Combine record o into record r.
+__device__ __forceinline__ void diag_combine(double* r, const volatile double* o) {
+  for (int c = 0; c < 5; ++c) r[c] += o[c];
+  r[5] = fmin(r[5], o[5]);
+  r[6] = fmax(r[6], o[6]);
+  r[7] = fmin(r[7], o[7]);
+  r[8] = fmax(r[8], o[8]);
+  r[9] = fmax(r[9], o[9]);
+  r[10] += o[10];
+}
+
+// The records of a block's threads (acc) reduced by a fixed tree into
+// sh[.][0]; ends with a barrier.
+__device__ __forceinline__ void diag_block_tree(const double* acc, double (*sh)[RED_THREADS]) {
+  for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) {
+      double r[DIAG_WORDS], o[DIAG_WORDS];
+      for (int c = 0; c < DIAG_WORDS; ++c) {
+        r[c] = sh[c][threadIdx.x];
+        o[c] = sh[c][threadIdx.x + half];
+      }
+      diag_combine(r, o);
+      for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = r[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Last block: combine the nb block records (in block order per thread, then
+// the fixed tree: the same order whichever block is last) and publish the
+// diagnostics of the state in the grid's device record.
+__device__ __forceinline__ void diag_finish(const double* partial, int nb, Scalars* sc, double (*sh)[RED_THREADS]) {
+  const volatile double* P = partial;
+  double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) diag_combine(r, P + (long long)b * DIAG_WORDS);
+  __syncthreads();
+  diag_block_tree(r, sh);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
+    sc->diag[9] = sqrt(sh[9][0]);  // maximum Mach number
+    jz_diag& o = sc->out;
+    o.time = sc->time;
+    o.step = sc->step;
+    o.dt = sc->dt;
+    for (int v = 0; v < 5; ++v) o.sum[v] = sc->diag[v];
+    o.rho_min = sc->diag[5];
+    o.rho_max = sc->diag[6];
+    o.p_min = sc->diag[7];
+    o.p_max = sc->diag[8];
+    o.mach_max = sc->diag[9];
+    o.nonfinite = (int64_t)sc->diag[10];
+  }
+}
+
+// Per-thread diagnostics accumulator of one state type.
+template <typename ST>
+struct DiagAcc {
+  RunSum<ST> sum[5];
+  ST rmin = ST(INFINITY), rmax = ST(-INFINITY), pmin = ST(INFINITY), pmax = ST(-INFINITY), m2max = ST(0);
+  double nonfinite = 0.0;
+  __device__ __forceinline__ void node(const ST q[5], ST Jn, ST gm1, ST g) {
+    bool finite = true;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) finite = finite && isfinite(q[v]);
+    if (!finite) {
+      nonfinite += 1.0;
+      return;
+    }
+    const ST vol = ST(1) / Jn;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sum[v].add(q[v] * vol);
+    ST p, m2;
+    diag_node<ST>(q, gm1, g, p, m2);
+    const ST rho = q[0];
+    rmin = rho < rmin ? rho : rmin;
+    rmax = rho > rmax ? rho : rmax;
+    pmin = p < pmin ? p : pmin;
+    pmax = p > pmax ? p : pmax;
+    m2max = m2 > m2max ? m2 : m2max;
+  }
+  __device__ __forceinline__ void record(double* acc) const {
+    for (int v = 0; v < 5; ++v) acc[v] = sum[v].value();
+    acc[5] = (double)rmin;
+    acc[6] = (double)rmax;
+    acc[7] = (double)pmin;
+    acc[8] = (double)pmax;
+    acc[9] = (double)m2max;
+    acc[10] = nonfinite;
+  }
+};
+
+// DIAG: every block also forms the diagnostics of the state it reads (its
+// record after the RED_BLOCKS rate partials) and the last block publishes
+// them, as k_diag does.
+template <typename ST, typename MT, bool DIAG = false>
 __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, const ST* __restrict__ Q,
                                               const MT* __restrict__ M, Scalars* sc, double* partial, double cfl,
                                               bool finalize = true) {
@@ -62,6 +161,7 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
   // the maximum is taken in the arithmetic type: exact, and the same value
   // as a maximum of the widened rates
   ST best_s = ST(0);
+  DiagAcc<ST> dg;
   // the nodes are taken as items of 32 consecutive i (item = ch + nch (j +
   // nj k), ch the chunk of i); warp w of the fixed grid takes items 4w ..
   // 4w + 3, then the next four after all warps, one node per lane and item,
@@ -122,6 +222,7 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
         }
         const ST rate = conv + ST(2) * nu * Jn * Jn * s2;
         best_s = rate > best_s ? rate : best_s;
+        if (DIAG) dg.node(q[u], Jn, gm1, g);
       }
     }
   }
@@ -135,7 +236,16 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
     for (int w = 1; w < RED_THREADS / 32; ++w) m = fmax(m, red[w]);
     partial[blockIdx.x] = m;
   }
+  __shared__ double sh[DIAG_WORDS][RED_THREADS];
+  if (DIAG) {
+    double acc[DIAG_WORDS];
+    dg.record(acc);
+    diag_block_tree(acc, sh);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < DIAG_WORDS; ++c) partial[RED_BLOCKS + (long long)blockIdx.x * DIAG_WORDS + c] = sh[c][0];
+  }
   if (last_block(&sc->count)) {  // max is exact in any order
+    if (DIAG) diag_finish(partial + RED_BLOCKS, (int)gridDim.x, sc, sh);
     double m = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, ((volatile double*)partial)[b]);
     m = warp_max(m);
@@ -158,11 +268,11 @@ __device__ __forceinline__ void timestep_body(const Layout& L, const FlowC& F, c
   }
 }
 
-template <typename ST, typename MT>
+template <typename ST, typename MT, bool DIAG = false>
 __global__ void __launch_bounds__(RED_THREADS) k_timestep(Layout L, FlowC F, const ST* __restrict__ Q,
                                                           const MT* __restrict__ M, Scalars* sc, double* partial,
                                                           double cfl, bool finalize) {
-  timestep_body<ST, MT>(L, F, Q, M, sc, partial, cfl, finalize);
+  timestep_body<ST, MT, DIAG>(L, F, Q, M, sc, partial, cfl, finalize);
 }
 
 // batched: grid blockIdx.y of the table; gridDim.x blocks per grid
@@ -212,18 +322,14 @@ __global__ void k_fixed_dt(Scalars* sc, double dt) {
   sc->step += 1;
 }
 
-// Diagnostics partial per thread / block:
-//   [0..4] sum Q_v/J, [5] rho min, [6] rho max, [7] p min, [8] p max,
-//   [9] max of the squared Mach number, [10] non-finite count.
-// Per-node arithmetic in the state's type; each lane takes four nodes of its
-// row at a time with all their loads issued first.
+// Diagnostics of the state (records as described above).  Per-node
+// arithmetic in the state's type; each lane takes four nodes of its row at a
+// time with all their loads issued first.
 template <typename ST, typename MT>
 __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const ST* __restrict__ Q,
                                                       const MT* __restrict__ M, Scalars* sc, double* partial) {
   const ST gm1 = flow_const<ST>(F.gm1, F.gm1_f), g = flow_const<ST>(F.gamma, F.gamma_f);
-  RunSum<ST> sum[5];
-  ST rmin = ST(INFINITY), rmax = ST(-INFINITY), pmin = ST(INFINITY), pmax = ST(-INFINITY), m2max = ST(0);
-  double nonfinite = 0.0;
+  DiagAcc<ST> dg;
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const int W = (gridDim.x * blockDim.x) >> 5;
@@ -241,93 +347,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
         Jn[u] = (ST)M[9 * L.npad + n];
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (ib + lane + 32 * u >= L.n[0]) continue;
-        bool finite = true;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) finite = finite && isfinite(q[u][v]);
-        if (!finite) { nonfinite += 1.0; continue; }
-        const ST vol = ST(1) / Jn[u];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sum[v].add(q[u][v] * vol);
-        ST p, m2;
-        diag_node<ST>(q[u], gm1, g, p, m2);
-        const ST rho = q[u][0];
-        rmin = rho < rmin ? rho : rmin;
-        rmax = rho > rmax ? rho : rmax;
-        pmin = p < pmin ? p : pmin;
-        pmax = p > pmax ? p : pmax;
-        m2max = m2 > m2max ? m2 : m2max;
-      }
+      for (int u = 0; u < U; ++u)
+        if (ib + lane + 32 * u < L.n[0]) dg.node(q[u], Jn[u], gm1, g);
     }
   }
-  double acc[DIAG_WORDS] = {sum[0].value(), sum[1].value(), sum[2].value(), sum[3].value(), sum[4].value(),
-                            (double)rmin, (double)rmax, (double)pmin, (double)pmax, (double)m2max, nonfinite};
+  double acc[DIAG_WORDS];
+  dg.record(acc);
   __shared__ double sh[DIAG_WORDS][RED_THREADS];
-  for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = acc[c];
-  __syncthreads();
-  for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
-    if ((int)threadIdx.x < half) {
-      int o = threadIdx.x + half;
-      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
-      sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
-      sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
-      sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
-      sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
-      sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
-      sh[10][threadIdx.x] += sh[10][o];
-    }
-    __syncthreads();
-  }
+  diag_block_tree(acc, sh);
   if (threadIdx.x == 0)
     for (int c = 0; c < DIAG_WORDS; ++c) partial[(long long)blockIdx.x * DIAG_WORDS + c] = sh[c][0];
   if (last_block(&sc->dcount)) {
-    // thread t combines block records t, t + 256, ... in order, then the same
-    // fixed tree as above: a fixed summation order whichever block is last
-    const volatile double* P = partial;
-    double r[DIAG_WORDS] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, INFINITY, -INFINITY, 0, 0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      const volatile double* x = P + (long long)b * DIAG_WORDS;
-      for (int c = 0; c < 5; ++c) r[c] += x[c];
-      r[5] = fmin(r[5], x[5]);
-      r[6] = fmax(r[6], x[6]);
-      r[7] = fmin(r[7], x[7]);
-      r[8] = fmax(r[8], x[8]);
-      r[9] = fmax(r[9], x[9]);
-      r[10] += x[10];
-    }
-    __syncthreads();
-    for (int c = 0; c < DIAG_WORDS; ++c) sh[c][threadIdx.x] = r[c];
-    __syncthreads();
-    for (int half = RED_THREADS / 2; half > 0; half >>= 1) {
-      if ((int)threadIdx.x < half) {
-        int o = threadIdx.x + half;
-        for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][o];
-        sh[5][threadIdx.x] = fmin(sh[5][threadIdx.x], sh[5][o]);
-        sh[6][threadIdx.x] = fmax(sh[6][threadIdx.x], sh[6][o]);
-        sh[7][threadIdx.x] = fmin(sh[7][threadIdx.x], sh[7][o]);
-        sh[8][threadIdx.x] = fmax(sh[8][threadIdx.x], sh[8][o]);
-        sh[9][threadIdx.x] = fmax(sh[9][threadIdx.x], sh[9][o]);
-        sh[10][threadIdx.x] += sh[10][o];
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      for (int c = 0; c < DIAG_WORDS; ++c) sc->diag[c] = sh[c][0];
-      sc->diag[9] = sqrt(sh[9][0]);  // maximum Mach number
-      jz_diag& o = sc->out;
-      o.time = sc->time;
-      o.step = sc->step;
-      o.dt = sc->dt;
-      for (int v = 0; v < 5; ++v) o.sum[v] = sc->diag[v];
-      o.rho_min = sc->diag[5];
-      o.rho_max = sc->diag[6];
-      o.p_min = sc->diag[7];
-      o.p_max = sc->diag[8];
-      o.mach_max = sc->diag[9];
-      o.nonfinite = (int64_t)sc->diag[10];
-      sc->dcount = 0;
-    }
+    diag_finish(partial, (int)gridDim.x, sc, sh);
+    if (threadIdx.x == 0) sc->dcount = 0;
   }
 }
 
@@ -335,22 +367,45 @@ __global__ void __launch_bounds__(RED_THREADS) k_diag(Layout L, FlowC F, const S
 
 cudaError_t launch_timestep(const GridDev& g, double cfl, double dt_fixed, cudaStream_t s) {
   if (cfl <= 0.0) {
+    if (g.step_diag) {  // the diagnostics of the step's state by their own pass
+      cudaError_t e = launch_diagnostics(g, s);
+      if (e != cudaSuccess) return e;
+    }
     k_fixed_dt<<<1, 1, 0, s>>>(g.sc, dt_fixed);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  const int nb = red_grid(2);
+  if (g.step_diag) {
+    switch (g.prec) {
+      case JZ_P64:
+        k_timestep<double, double, true><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
+                                                                   (const double*)g.M, g.sc, g.partial, cfl, true);
+        break;
+      case JZ_P32_M64:
+        k_timestep<float, double, true><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
+                                                                  (const double*)g.M, g.sc, g.partial, cfl, true);
+        break;
+      default:
+        k_timestep<float, float, true><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
+                                                                 g.sc, g.partial, cfl, true);
+        break;
+    }
     count_launches(1);
     return cudaGetLastError();
   }
   switch (g.prec) {
     case JZ_P64:
-      k_timestep<double, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0,
-                                                                    (const double*)g.M, g.sc, g.partial, cfl, true);
+      k_timestep<double, double><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const double*)g.Q0, (const double*)g.M, g.sc,
+                                                            g.partial, cfl, true);
       break;
     case JZ_P32_M64:
-      k_timestep<float, double><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0,
-                                                                   (const double*)g.M, g.sc, g.partial, cfl, true);
+      k_timestep<float, double><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const double*)g.M, g.sc,
+                                                           g.partial, cfl, true);
       break;
     default:
-      k_timestep<float, float><<<red_grid(2), RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M,
-                                                                  g.sc, g.partial, cfl, true);
+      k_timestep<float, float><<<nb, RED_THREADS, 0, s>>>(g.L, g.F, (const float*)g.Q0, (const float*)g.M, g.sc,
+                                                          g.partial, cfl, true);
       break;
   }
   count_launches(1);

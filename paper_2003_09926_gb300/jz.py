@@ -69,6 +69,8 @@ def lib() -> C.CDLL:
             "jz_nsteps": ([G, C.c_int, C.c_double, C.c_double], C.c_int),
             "jz_diagnostics": ([G, C.POINTER(Diag)], C.c_int),
             "jz_diagnostics_async": ([G, VP], C.c_int),
+            "jz_set_step_diagnostics": ([G, C.c_int], C.c_int),
+            "jz_step_diagnostics_async": ([G, VP], C.c_int),
             "jz_state_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_state_upload": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
             "jz_metrics_download": ([G, C.POINTER(C.c_double), C.c_size_t], C.c_int),
@@ -225,7 +227,7 @@ def diag_dict(d: Diag) -> dict:
 
 class PinnedDiag:
     """A jz_diag record in page-locked host memory (a pinned torch tensor), the
-    target of Grid.diagnostics_async."""
+    target of Grid.diagnostics_async and Grid.step_diagnostics_async."""
 
     def __init__(self):
         torch = _torch()
@@ -392,6 +394,17 @@ class Grid:
         """Enqueue the diagnostics and their copy into out on the grid's
         stream (no synchronisation; read out after the stream passes it)."""
         _check(lib().jz_diagnostics_async(self.h, C.c_void_p(out.ptr)))
+
+    def set_step_diagnostics(self, on: bool) -> None:
+        """Let every later CFL step's time-step reduction also form the
+        diagnostics of the state the step starts from."""
+        _check(lib().jz_set_step_diagnostics(self.h, int(bool(on))))
+
+    def step_diagnostics_async(self, out: "PinnedDiag") -> None:
+        """Enqueue the copy of the latest diagnostics record (after a step
+        with step diagnostics on: the state that step started from) into
+        out, without a pass over the grid."""
+        _check(lib().jz_step_diagnostics_async(self.h, C.c_void_p(out.ptr)))
 
     def download(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:
