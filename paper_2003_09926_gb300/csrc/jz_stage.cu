@@ -34,7 +34,9 @@
 //  - i and j face fluxes go through shared memory, the k face flux of a
 //    column stays in its thread's registers;
 //  - the residual of plane t is completed and Q^(l) written with J and
-//    Q^(0) held in registers.
+//    Q^(0) held in registers;
+//  - every configuration is compiled for the Smagorinsky flow model of the
+//    workloads with constant flags and once with the flags read at run time.
 #include <cmath>
 #include <cstdint>
 

@@ -12,25 +12,29 @@
 // inviscid minus viscous flux: the paper's central difference plus
 // dissipation, telescoping exactly.
 //
-// Organisation (one CTA per SM, 2.5-D streaming over a TI x TJ (i, j) tile
-// and a chunk of k-planes; the file is compiled once per tile shape the
-// autotuner chooses from: 32 x 16, 16 x 32 and 16 x 16, VR_TI / VR_TJ, and
-// its entry points carry the shape in their names):
+// Organisation (2.5-D streaming over a TI x TJ (i, j) tile and a chunk of
+// k-planes; the file is compiled once per tile shape the autotuner chooses
+// from: 16 x 16 (the default, two CTAs per SM), 32 x 16 and 16 x 32 (one CTA
+// per SM), VR_TI / VR_TJ, and its entry points carry the shape in their
+// names; within a shape, once per flow model with the model's flags as
+// constants plus once with the flags read at run time, and within a build
+// once per node role):
 //  - TMA stages the conserved variables of one plane (tile plus a two-node
 //    halo) into a planar buffer, and the metric fields of one plane (tile
 //    plus a one-node halo) into a second buffer; waits are bounded;
 //  - each staged plane is converted once into two rings of node records:
-//    conserved (rho, rho u, rho v, rho w | e) and primitive (u, v, w, T | p),
-//    each a float4 plus a float over four planes, so that a node's stencil
-//    values arrive with two shared-memory loads;
+//    conserved (rho, rho u, rho v, rho w | e) over four planes and primitive
+//    (u, v, w, T | p) over three, each a float4 plus a float, so that a
+//    node's stencil values arrive with two shared-memory loads;
 //  - one thread per node of the plus-shaped set (tile nodes plus the
 //    one-node i and j halo) forms G^k, the dissipation radius lambda~^k and
 //    the sensor nu^k of its node (tile threads in all three directions, halo
 //    threads in their own direction);
 //  - i and j face fluxes go through shared memory as float4 + float records,
 //    the k face flux of a column stays in its thread's registers;
-//  - three block barriers per plane: node pass | i, j and k face fluxes |
-//    residual, update and conversion of the plane three ahead.
+//  - two block barriers per plane: node pass of plane t+1, k face, i/j
+//    residual and update of plane t | i/j face fluxes of plane t+1 and the
+//    conversion of the plane three ahead.
 #include <cmath>
 #include <cstdint>
 
