@@ -754,11 +754,14 @@ def main(argv=None):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.upload(host_in)
+    g.upload(host_in)  # synchronous, like the download
+    t1 = time.perf_counter()
     seen = run(args.steps)
+    t2 = time.perf_counter()
     g.download(host_out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    e2e_s = t3 - t0
     assert len(seen) == args.steps + 1 and all(d["nonfinite"] == 0 for d in seen)
     assert [d["step"] for d in seen] == list(range(seen[0]["step"], seen[0]["step"] + args.steps + 1))
     e2e_s = reduce_max(torch, e2e_s, world, "cuda")
@@ -767,6 +770,7 @@ def main(argv=None):
     e2e = {"value": weak_value(pts, args.steps, 1e3 * e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / args.steps,
            "d2h_bytes_per_step": (diag_bytes + state_bytes) / args.steps,
+           "split_ms": {"upload": 1e3 * (t1 - t0), "steps": 1e3 * (t2 - t1), "download": 1e3 * (t3 - t2)},
            "note": "initial state uploaded from pinned host memory; every step's diagnostics (of the state the "
                    "step starts from, formed by its time-step reduction) copied to pinned host memory and read "
                    "one step behind; the final state's diagnostics by one pass; final state downloaded"}
