@@ -286,8 +286,9 @@ int jz_diagnostics_async(jz_grid* g, jz_diag* out);
  * step is read with jz_step_diagnostics_async.  Its sums are accumulated in
  * another order than those of jz_diagnostics (equal up to rounding); its
  * extrema and non-finite count are the same.  The stepping itself is
- * unchanged.  on = 0 (the default) switches it off.  JZ_EINVAL for other
- * values of on. */
+ * unchanged.  Affects single-grid steps only (jz_rk_step, jz_nsteps);
+ * batches and the per-block entry points ignore it.  on = 0 (the default)
+ * switches it off.  JZ_EINVAL for other values of on. */
 int jz_set_step_diagnostics(jz_grid* g, int on);
 
 /* Enqueue on the grid's stream the copy of the grid's latest diagnostics
