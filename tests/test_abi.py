@@ -71,6 +71,9 @@ def test_create_rejects_bad_buffers_without_cuda(L):
 def test_null_handles_rejected(L):
     assert L.jz_rk_step(None, 0.5, 0.0) == jz.JZ_EINVAL
     assert L.jz_grid_destroy(None) == jz.JZ_OK
+    assert L.jz_set_step_diagnostics(None, 1) == jz.JZ_EINVAL
+    assert L.jz_step_diagnostics_async(None, None) == jz.JZ_EINVAL
+    assert L.jz_diagnostics_async(None, None) == jz.JZ_EINVAL
     n = C.c_uint64()
     assert L.jz_launch_count(C.byref(n)) == jz.JZ_OK
 
