@@ -551,7 +551,8 @@ def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 256, ba
     case (the configuration's 2e7 by default), 50..500 steps, Poisson
     arrivals at 70% of the measured batched capacity, 150 GB HBM budget.
     Headline: prioritised streams (at most 2 resident cases, the oldest on
-    the highest-priority stream, 20-step chunks); optionally the time-slice
+    the highest-priority stream, 20-step chunks, a case joining the oldest
+    only while its work is at most a quarter of the oldest's remaining work); optionally the time-slice
     server with batched launches in the given slice orders; against the
     same trace served one case at a time in FP32, and in plain FP64 on its
     first cases with the full trace extrapolated at the FP64 rate measured
@@ -563,11 +564,12 @@ def bench_serving(jz, torch, W, local: int, capacity: float, nreq: int = 256, ba
     trace = serve.poisson_trace(cfg, rate)
     out = {"workload": f"c4 trace: {nreq} cases, log-uniform 1e5..{pts_hi:.0e} points, 50..500 steps, seed 4",
            "arrival_rate_hz": rate, "budget_bytes": 150 * 10**9}
-    srv = serve.PriorityServer(150 * 10**9, max_running=2, chunk_steps=20, device=local)
+    srv = serve.PriorityServer(150 * 10**9, max_running=2, chunk_steps=20, device=local, fill_ratio=0.25)
     out["fp32_continuous_priority_streams"] = dict(
-        serve.summarize(srv.run(trace)), max_running=2, chunk_steps=20, chunks=srv.chunks,
+        serve.summarize(srv.run(trace)), max_running=2, chunk_steps=20, fill_ratio=0.25, chunks=srv.chunks,
         peak_resident_bytes=srv.peak_bytes,
-        policy="cases admitted in arrival order as memory and one of 2 slots free up; each advances with its own "
+        policy="cases admitted in arrival order as memory and one of 2 slots free up, a case beside the oldest "
+               "only while its work is at most 0.25 of the oldest's remaining work; each advances with its own "
                "graph-replayed steps, 20 at a time, on the stream of its arrival rank (oldest = highest priority), "
                "so later cases run in the capacity the oldest leaves idle")
     for order in orders:

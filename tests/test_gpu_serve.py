@@ -94,7 +94,8 @@ def test_priority_server_results_same_alone_and_in_the_mix(mods):
     jz, serve = mods
     reqs = _trace(serve)
     sizes = sorted(jz.jz_grid_bytes(r.grid) for r in reqs)
-    srv = serve.PriorityServer(sizes[-1] + sizes[-2] + sizes[-3], max_running=3, chunk_steps=4, keep_state=True)
+    srv = serve.PriorityServer(sizes[-1] + sizes[-2] + sizes[-3], max_running=3, chunk_steps=4, keep_state=True,
+                               fill_ratio=None)  # every case may overlap the oldest
     res = srv.run(reqs)
     assert all(r.status == "done" for r in res) and srv.chunks >= sum((q.steps + 3) // 4 for q in reqs)
     for r, q in zip(res, reqs):

@@ -187,7 +187,7 @@ def test_priority_server_ranks_streams_by_arrival():
     when it finishes, the next one moves up (at a chunk boundary)."""
     be = FakeBackend()
     reqs = [_req(0, 10, 40), _req(1, 10, 100), _req(2, 10, 60)]
-    srv = serve.PriorityServer(10 ** 6, max_running=3, chunk_steps=10, backend=be)
+    srv = serve.PriorityServer(10 ** 6, max_running=3, chunk_steps=10, backend=be, fill_ratio=None)
     res = srv.run(reqs)
     assert all(r.status == "done" for r in res) and [r.diag["step"] for r in res] == [40, 100, 60]
     assert be.grids[0].stream == "s0"
@@ -207,3 +207,24 @@ def test_priority_server_budget_slots_and_cancel():
     assert res[1].status == "done" and res[2].status == "done"
     assert srv.peak_bytes == 1000
     assert be.log.index(("close", 0)) < be.log.index(("create", 1)) < be.log.index(("create", 2))
+
+
+def test_priority_server_fills_only_with_small_work():
+    """With fill_ratio, a case joins the resident oldest one only while its
+    work is at most fill_ratio times the oldest's remaining work; a larger
+    one waits (admission stays in arrival order, so the cases behind it
+    wait too) until the oldest has retired."""
+    be = FakeBackend()
+    # case 0: 20^3 nodes x 200 steps; case 1: 10^3 x 40 (small: joins at
+    # once); case 2: 20^3 x 200 (large: waits for case 0)
+    reqs = [_req(0, 20, 200), _req(1, 10, 40), _req(2, 20, 200)]
+    srv = serve.PriorityServer(10 ** 9, max_running=2, chunk_steps=20, backend=be, fill_ratio=0.25)
+    res = srv.run(reqs)
+    assert all(r.status == "done" for r in res)
+    log = be.log
+    assert log.index(("create", 1)) < log.index(("close", 0))  # filled in beside case 0
+    assert log.index(("close", 0)) < log.index(("create", 2))  # held until case 0 retired
+    # without the limit, the second slot takes case 2 as soon as case 1 retires
+    be2 = FakeBackend()
+    serve.PriorityServer(10 ** 9, max_running=2, chunk_steps=20, backend=be2, fill_ratio=None).run(reqs)
+    assert be2.log.index(("create", 2)) < be2.log.index(("close", 0))
